@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark of the two-component D2Q9 Shan-Chen LB time step on GB300.
+
+Workload (N = 1): 1024 x 2048 grid, FP32 populations, tau 1, G 1.4 (immiscible),
+masses 1.0 / 0.9, g 1e-5, 8-mode interface; one benchmark step = 100 LB time
+steps plus one diagnostics evaluation (energy-budget terms every 100 steps).
+The metric is MLUPS (million lattice-site updates per second; one update
+advances both components).  Population buffers (2 x 151 MB) exceed the 129 MB
+L2, so no separate L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage f32|f16|bf16] [--kernel fused|two_pass] [--tile-y T]
+
+--impl reference times the FP64 CPU oracle on the host on a bounded sample of
+the same workload.  With torchrun (N > 1) every rank advances its own
+independent realisation (replicas, no collective on the data path); the time is
+the maximum over ranks and the value is the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+LB_STEPS_PER_STEP = 100
+BYTES_PER_SITE = {"f32": 144, "f16": 72, "bf16": 72}   # 18 loads + 18 stores per site update
+METRIC = "MLUPS & HBM-roofline %; plain FP32 vs FP16-store/ensemble/learned @ stated err"
+PROFILE_TRAFFIC = ROOT / "profiles" / "traffic.json"
+
+
+def workload(args) -> dict:
+    return dict(nx=args.nx, ny=args.ny, tau_A=1.0, tau_B=1.0, G=1.4, mass_A=1.0, mass_B=0.9, g=1e-5,
+                n_modes=8, amp=2.0, width=1.5, minority=0.08, crop_rows=10)
+
+
+def config_of(args, n_gpus) -> dict:
+    return {
+        "workload": f"{args.nx}x{args.ny} two-component D2Q9 Shan-Chen Rayleigh-Taylor, G=1.4, tau=1, "
+                    f"{args.storage} populations, diagnostics every {LB_STEPS_PER_STEP} steps",
+        "nx": args.nx, "ny": args.ny, "lb_steps_per_step": LB_STEPS_PER_STEP,
+        "storage": args.storage, "kernel": args.kernel, "tile_y": args.tile_y,
+        "l2": "inputs larger than L2 (two population buffers of "
+              f"{args.nx * args.ny * BYTES_PER_SITE[args.storage] // 2 / 1e6:.0f} MB each vs 129 MB L2)",
+        "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_2101_04847_gb300" / "csrc").glob("*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_name: str, nx: int, ny: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, scaled
+    to this grid; None when absent or taken on a different kernel source."""
+    try:
+        d = json.loads(PROFILE_TRAFFIC.read_text())
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_name)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"] * (nx * ny) / (e["nx"] * e["ny"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"bench_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in self.path.read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            self.path.unlink()
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    try:
+        d = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2101_04847_gb300 import lbm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    params = workload(args)
+    params["seed"] = 1 + rank
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        solver = lbm.Solver(storage=args.storage, kernel=args.kernel, tile_y=args.tile_y, **params)
+    sites = args.nx * args.ny
+    launches_per_step = LB_STEPS_PER_STEP * (2 if args.kernel == "two_pass" else 1) + 5
+
+    def one_step(ev_pair=None):
+        if ev_pair is not None:
+            ev_pair[0].record(stream)
+        solver.step(LB_STEPS_PER_STEP)
+        if ev_pair is not None:
+            ev_pair[1].record(stream)
+        solver.diagnostics()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    step_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0.record(stream)
+        for k in range(args.steps):
+            one_step(step_events[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in step_events) / (args.steps * LB_STEPS_PER_STEP)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms, kernel_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, kernel_ms = t.tolist()
+    total_sites = sites * LB_STEPS_PER_STEP * args.steps * ws
+    mlups = total_sites / (elapsed_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: populations in from pinned host
+    # memory, 100 steps, diagnostics back to the host, every step
+    host = torch.empty((2, 9, args.ny, args.nx), dtype=torch.float64, pin_memory=True).numpy()
+    solver.populations(out=host)
+    for _ in range(2):
+        solver.set_populations(host)
+        solver.step(LB_STEPS_PER_STEP)
+        solver.diagnostics()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_populations(host)
+        solver.step(LB_STEPS_PER_STEP)
+        solver.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e_mlups = sites * LB_STEPS_PER_STEP * e2e_steps * ws / e2e_s / 1e6
+    nrows = args.ny - 2 * params["crop_rows"]
+    solver.close()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak_hbm()
+    bytes_per_launch = BYTES_PER_SITE[args.storage] * sites
+    achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
+    kname = "step_fused_kernel" if args.kernel == "fused" else "collide_kernel"
+    traffic = profiled_traffic(f"{kname}:{args.storage}", args.nx, args.ny)
+    out = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": config_of(args, ws),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": kname, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "launch_ms": round(kernel_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
+        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": 18 * sites * 8,
+                "d2h_bytes_per_step": (15 + nrows) * 8 + 4},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, budget_s: float) -> dict:
+    """The FP64 numpy oracle as it stands, on the host, one LB step at a time on the full
+    grid until about `budget_s` seconds of CPU work are done."""
+    from oracle import lbm_oracle as O
+
+    p = O.Params(**workload(args))
+    f = O.initial_populations(p)
+    f = O.step(f, p, 1)  # warm-up
+    n = 0
+    t = time.perf_counter()
+    while True:
+        f = O.step(f, p, 1)
+        n += 1
+        if time.perf_counter() - t > budget_s and n >= 2:
+            break
+    dt = time.perf_counter() - t
+    return {"value": round(args.nx * args.ny * n / dt / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} LB steps of the full {args.nx}x{args.ny} grid (FP64 numpy, single thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import lbm_oracle as O
+
+    p = O.Params(**workload(args))
+    f = O.initial_populations(p)
+    for _ in range(args.warmup):
+        f = O.step(f, p, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.step(f, p, 1)
+    dt = time.perf_counter() - t
+    mlups = args.nx * args.ny * args.steps / dt / 1e6
+    out = {
+        "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, ws), "impl": "reference",
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step is 1 LB step of the full {args.nx}x{args.ny} grid "
+                                   "(FP64 numpy oracle, single thread)"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--kernel", choices=["fused", "two_pass"], default="fused")
+    ap.add_argument("--tile-y", dest="tile_y", type=int, default=0)
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

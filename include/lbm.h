@@ -1,0 +1,193 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) two-component D2Q9 Shan-Chen lattice
+ * Boltzmann solver for 2D Rayleigh-Taylor turbulence.
+ *
+ * The method is the one of Tavares, Biferale, Sbragaglia and Mailybaev,
+ * "Validation and application of the lattice Boltzmann algorithm for a
+ * turbulent immiscible Rayleigh-Taylor system" (arXiv 2101.04847):
+ *   - densities and common velocity: Section 2, Eq. (1);
+ *   - forced BGK kinetic equation: Section 2, Eq. "Kinetic equation";
+ *   - shifted-velocity equilibrium: Section 2, Eq. "Equilibrium distribution";
+ *   - Shan-Chen fluid-fluid force (psi = rho, no self-interaction):
+ *     Section 2, Eq. "Shan-Chen forcing term";
+ *   - fluid-boundary force: Section 2, Eq. after the Shan-Chen force;
+ *   - Boussinesq buoyancy: Section 2, Eq. (3_Fex);
+ *   - periodic x, solid bottom/top with bounce-back: Section 2, last paragraph;
+ *   - energies, energy budget, stress split, interface length and enstrophy:
+ *     Section 3 (Eqs. "Kinetic energy balance", "Three parts of the pressure
+ *     tensor", "Korteweg stress and total length", "Dissipation function").
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an lbm_status; nothing throws across the ABI.
+ *     lbm_last_error() gives a human-readable message for the calling thread.
+ *   - Grids are nx (periodic, x) by ny (walls, y); y = 0 is the bottom wall row
+ *     and y = ny-1 the top wall row.  Component A (index 0) is the heavy fluid
+ *     on top, B (index 1) the light fluid below.  Directions:
+ *     0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1).
+ *   - Host arrays are C-contiguous double arrays, row-major [y][x]; population
+ *     arrays are [component][direction][y][x] and hold the post-streaming
+ *     populations f_i^s(x, t) of the kinetic equation (the values whose sums are
+ *     the densities of Eq. (1)).
+ *   - Ownership: a device workspace or stream passed in is borrowed; the caller
+ *     keeps it alive until lbm_destroy.  With a NULL workspace the library
+ *     allocates (cudaMalloc) and frees its own.
+ *   - Threads: one handle is used by one host thread at a time.
+ *   - Work is queued asynchronously on the handle's stream; the calls that return
+ *     data to the host (diagnostics, fields, populations, save) synchronise it.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* invalid argument or parameter set */
+    LBM_ENOMEM = 2,     /* allocation failed or workspace too small */
+    LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
+    LBM_EUNSTABLE = 4,  /* sticky: a NaN or negative density was seen by the step */
+    LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LBM_ESTATE = 6,     /* call not valid in the handle's current state */
+    LBM_EIO = 7         /* file I/O error (save/load) */
+} lbm_status;
+
+typedef enum {
+    LBM_STORE_F32 = 0,   /* populations stored as float */
+    LBM_STORE_F16 = 1,   /* stored as half, shifted: h = f - w_i rho0_s */
+    LBM_STORE_BF16 = 2   /* stored as bfloat16, shifted: h = f - w_i rho0_s */
+} lbm_storage;
+
+typedef enum {
+    LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step */
+    LBM_KERNEL_TWO_PASS = 1  /* density kernel + stream-collide kernel per step */
+} lbm_kernel;
+
+/* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
+typedef struct {
+    int32_t nx, ny;          /* grid; nx >= 4, ny >= 8 */
+    double tau_A, tau_B;     /* BGK relaxation times, > 0.5 (kinematic viscosity cs^2 (tau - 1/2)) */
+    double G;                /* G_AB of the Shan-Chen force */
+    double G_wall_A;         /* G_Ab of the fluid-boundary force (0 = neutral wetting) */
+    double G_wall_B;         /* G_Bb */
+    double mass_A, mass_B;   /* bulk density of pure A (top) and pure B (bottom), > 0 */
+    double g;                /* g~ of Eq. (3_Fex) */
+    int32_t gravity_mode;    /* 0: F_A = -rho_A g e_y, F_B = +rho_B g e_y (Eq. 3_Fex); 1: -rho_s g e_y for both */
+    double gx;               /* uniform body acceleration along x (validation cases) */
+    uint64_t seed;           /* interface perturbation seed (splitmix64) */
+    int32_t n_modes;         /* number of sinusoidal modes of the interface perturbation, 0..64 */
+    double amp;              /* perturbation amplitude in cells */
+    double width;            /* tanh half-width of the initial interface, > 0 */
+    double minority;         /* fraction of the other component in each bulk, [0, 1) */
+    double y0;               /* mean interface height; < 0 means ny / 2 */
+    int32_t crop_rows;       /* rows cut at top and bottom for averages, >= 3, 2*crop_rows < ny - 2 */
+    int32_t storage;         /* lbm_storage */
+    int32_t kernel;          /* lbm_kernel */
+    int32_t tile_y;          /* rows per block of the fused kernel; 0 = default */
+    double shift_A, shift_B; /* rho0_s of the shifted storage; <= 0 means (mass_s (1 + minority)) / 2 */
+} lbm_params;
+
+/* Diagnostics of one state (Section 3).  Averages <.> run over the sub-domain
+ * without crop_rows rows at each wall; u is the physical velocity
+ * (sum_{s,i} f c + (F_A + F_B)/2) / rho. */
+typedef struct {
+    int64_t step;        /* time step of the state */
+    double mass_A;       /* sum of rho_A over the whole grid */
+    double mass_B;       /* sum of rho_B over the whole grid */
+    double E_k;          /* <rho |u|^2 / 2> */
+    double E_p;          /* g <y phi>, phi = rho_A - rho_B */
+    double buoyancy;     /* g <u_y phi> */
+    double flux_pb;      /* <u . grad p_b>, p_b = cs^2 rho + G cs^2 (rho^2 - phi^2) / 4 */
+    double flux_K;       /* <u . div P^K> (Korteweg stress, kappa = cs^4 G / 4) */
+    double flux_tau;     /* <u . div K^(tau)> (spurious tau-dependent stress) */
+    double viscous;      /* <u . div(eta grad u + eta grad u^T)>, eta = rho_bar cs^2 (tau - 1/2) */
+    double enstrophy;    /* (1/2) sum omega^2 over the sub-domain */
+    double rho_bar;      /* <rho> */
+    double h;            /* mixing-layer width 6 sum_y c (1 - c) of the normalised row-mean phi */
+    double L_int;        /* interface length, 4-direction Cauchy-Crofton estimate */
+    int64_t cc[4];       /* sign changes of (phi > 0) along 0, 90, 45, 135 degrees */
+    int32_t status;      /* LBM_OK or LBM_EUNSTABLE */
+} lbm_diag;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Library version string. */
+const char* lbm_version(void);
+
+/* Text of a status code; never NULL. */
+const char* lbm_status_str(lbm_status st);
+
+/* Message of the last failing call on this thread; "" if none. */
+const char* lbm_last_error(void);
+
+/* Fill *p with the defaults: 128 x 256, tau 1, G 1.4, masses 1.0 / 0.9,
+ * g 1e-5, Boussinesq gravity, 8 modes of amplitude 2, width 1.5, minority 0.08,
+ * crop 10, FP32 fused.  Returns LBM_EINVAL if p is NULL. */
+lbm_status lbm_params_default(lbm_params* p);
+
+/* Bytes of device workspace lbm_create_ex needs for *p. */
+lbm_status lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
+
+/* Create a solver with the defaults overridden by the arguments, on the current
+ * device, with its own workspace and stream, initialised to the perturbed
+ * interface (Section 2, last paragraph).  LBM_EINVAL on an invalid parameter. */
+lbm_status lbm_create(int32_t nx, int32_t ny, double tau, double G, double mass_A,
+                      double mass_B, double g, uint64_t seed, lbm_handle** out);
+
+/* Create a solver from a full parameter set.  dev_workspace: NULL, or a device
+ * buffer of at least lbm_workspace_bytes(p) bytes, 256-byte aligned, borrowed.
+ * cuda_stream: a cudaStream_t to queue work on, or NULL for a stream owned by
+ * the handle.  The state is initialised as in lbm_create. */
+lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_bytes,
+                         void* cuda_stream, lbm_handle** out);
+
+/* Re-initialise the state to step 0 (the initial condition of the parameters). */
+lbm_status lbm_reset(lbm_handle* h);
+
+/* Advance nsteps >= 0 time steps of the kinetic equation (Section 2): pull
+ * streaming with periodic x and half-way bounce-back walls, densities and common
+ * velocity (Eq. 1), Shan-Chen + wall + buoyancy forces, forced BGK collision.
+ * Asynchronous; returns LBM_EUNSTABLE only if an earlier sync saw it. */
+lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Wait for the queued work; LBM_EUNSTABLE if a NaN / negative density was seen. */
+lbm_status lbm_sync(lbm_handle* h);
+
+/* Current time step of the state. */
+lbm_status lbm_step_count(lbm_handle* h, int64_t* step);
+
+/* Diagnostics of the current state (Section 3); synchronises.  *out is filled
+ * even when the returned status is LBM_EUNSTABLE. */
+lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out);
+
+/* Row means of phi = rho_A - rho_B over rows [crop_rows, ny - crop_rows) from
+ * the last lbm_diagnostics call: ny - 2 crop_rows doubles written to host_rows. */
+lbm_status lbm_profile(lbm_handle* h, double* host_rows);
+
+/* rho_A, rho_B and the physical velocity components on the whole grid, nx*ny
+ * doubles each, host pointers ([y][x]); any of them may be NULL. */
+lbm_status lbm_get_fields(lbm_handle* h, double* rhoA, double* rhoB, double* ux, double* uy);
+
+/* Post-streaming populations, 2*9*ny*nx doubles, host pointer. */
+lbm_status lbm_get_populations(lbm_handle* h, double* host);
+
+/* Replace the state by the given post-streaming populations (2*9*ny*nx doubles,
+ * host pointer), rounded to the storage type.  The step counter is kept. */
+lbm_status lbm_set_populations(lbm_handle* h, const double* host);
+
+/* Write the raw stored state (header + populations) to a file / read it back
+ * into a handle created with the same nx, ny and storage.  Bitwise round trip. */
+lbm_status lbm_save(lbm_handle* h, const char* path);
+lbm_status lbm_load(lbm_handle* h, const char* path);
+
+/* Release the handle (and its own workspace / stream if it allocated them). */
+void lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,63 @@
+// Device helpers shared by the kernels of liblbm: storage conversion of the
+// populations and the pull of the post-streaming populations of one site.
+// A buffer B holds post-collision populations in structure-of-arrays layout
+// [component][direction][y][pitch]; the post-streaming population of the kinetic
+// equation (Section 2 of arXiv 2101.04847) is
+//     S_i(x, y) = B_i(x - c_ix, y - c_iy)   if 0 <= y - c_iy < ny  (x periodic)
+//     S_i(x, y) = B_opp(i)(x, y)            otherwise (half-way bounce-back)
+#pragma once
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// storage types: float, or half / bfloat16 holding f - w_i rho0_s
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T> struct IsShifted { static constexpr bool value = true; };
+template <> struct IsShifted<float> { static constexpr bool value = false; };
+
+template <typename T>
+__device__ __forceinline__ float load_pop(const T* p, int i, float shift_s) {
+    float v = to_f<T>(__ldg(p));
+    if (IsShifted<T>::value) v += wf(i) * shift_s;
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ void store_pop(T* p, int i, float v, float shift_s) {
+    if (IsShifted<T>::value) v -= wf(i) * shift_s;
+    *p = from_f<T>(v);
+}
+
+// Pull the 18 post-streaming populations of column xc (neighbours xm, xp) on row y.
+template <typename T>
+__device__ __forceinline__ void pull_site(const T* __restrict__ fin, const Grid& g, const float shift[2],
+                                          int y, int xc, int xm, int xp, float f[2][9]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sy = y - cy(i);
+            const int sx = cx(i) == 0 ? xc : (cx(i) == 1 ? xm : xp);
+            const bool inside = (cy(i) == 0) || (sy >= 0 && sy < g.ny);
+            const size_t idx = inside
+                ? (size_t)(s * 9 + i) * g.plane + (size_t)sy * g.pitch + sx
+                : (size_t)(s * 9 + opp(i)) * g.plane + (size_t)y * g.pitch + xc;
+            f[s][i] = load_pop<T>(fin + idx, i, shift[s]);
+        }
+    }
+}
+
+__device__ __forceinline__ float sum9(const float* f) {
+    return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+}
+
+}  // namespace lbm

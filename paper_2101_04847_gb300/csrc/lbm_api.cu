@@ -1,0 +1,590 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// workspace layout, stream and CUDA-graph management, diagnostics assembly,
+// host transfers and checkpoints.  All compute runs in the kernels of
+// step_kernels.cu and diag_kernels.cu.
+#include "lbm_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lbm_status fail(lbm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return LBM_ECUDA;
+}
+
+#define LBM_TRY(call, what)                                \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int kGraphChunk = 50;   // steps per captured CUDA graph
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t elem_size(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------------------
+// splitmix64 (Steele, Lea, Flood, OOPSLA 2014) for the interface perturbation
+// ---------------------------------------------------------------------------
+uint64_t splitmix64_next(uint64_t& state) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double unit_double(uint64_t v) { return (double)(v >> 11) * (1.0 / 9007199254740992.0); }
+
+// Interface height y0(x) = base + amp * eta(x) / max|eta|,
+// eta(x) = sum_{m=1..M} a_m sin(2 pi m x / nx + theta_m), draws a_1, theta_1, a_2, ...
+std::vector<double> interface_height(const lbm_params& p) {
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<double> a(p.n_modes), th(p.n_modes);
+    uint64_t st = p.seed;
+    for (int m = 0; m < p.n_modes; ++m) {
+        a[m] = unit_double(splitmix64_next(st));
+        th[m] = two_pi * unit_double(splitmix64_next(st));
+    }
+    std::vector<double> eta(p.nx, 0.0);
+    double peak = 0.0;
+    for (int x = 0; x < p.nx; ++x) {
+        double e = 0.0;
+        for (int m = 0; m < p.n_modes; ++m) e += a[m] * std::sin(two_pi * (m + 1) * x / p.nx + th[m]);
+        eta[x] = e;
+        peak = std::fmax(peak, std::fabs(e));
+    }
+    const double base = p.y0 < 0.0 ? p.ny / 2.0 : p.y0;
+    std::vector<double> y0(p.nx);
+    for (int x = 0; x < p.nx; ++x) y0[x] = peak > 0.0 ? base + p.amp * eta[x] / peak : base;
+    return y0;
+}
+
+struct Layout {
+    size_t pops[2], psi, scratch, partials, out, flag, y0, total;
+    size_t pop_bytes, plane;
+    int pitch;
+};
+
+Layout make_layout(const lbm_params& p) {
+    Layout L;
+    L.pitch = (p.nx + 63) / 64 * 64;
+    L.plane = (size_t)p.ny * L.pitch;
+    L.pop_bytes = 18 * L.plane * elem_size(p.storage);
+    const size_t n = (size_t)p.nx * p.ny;
+    size_t off = 0;
+    L.pops[0] = off; off = align_up(off + L.pop_bytes);
+    L.pops[1] = off; off = align_up(off + L.pop_bytes);
+    L.psi = off; off = align_up(off + 2 * L.plane * sizeof(float));
+    const size_t scratch_d = std::max(lbm::diag_scratch_doubles(p.nx, p.ny), (size_t)18 * n);
+    L.scratch = off; off = align_up(off + scratch_d * sizeof(double));
+    L.partials = off; off = align_up(off + lbm::diag_partials_doubles(p.nx, p.ny) * sizeof(double));
+    L.out = off; off = align_up(off + (lbm::kDiagTerms + (size_t)p.ny) * sizeof(double));
+    L.flag = off; off = align_up(off + 16);
+    L.y0 = off; off = align_up(off + (size_t)p.nx * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+lbm_status validate(const lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 4 || p->ny < 8) return fail(LBM_EINVAL, "nx must be >= 4 and ny >= 8");
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return fail(LBM_EINVAL, "nx*ny must be < 2^31");
+    if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return fail(LBM_EINVAL, "tau must be > 0.5");
+    if (!(p->mass_A > 0.0) || !(p->mass_B > 0.0)) return fail(LBM_EINVAL, "masses must be > 0");
+    if (!(p->width > 0.0)) return fail(LBM_EINVAL, "width must be > 0");
+    if (!(p->minority >= 0.0 && p->minority < 1.0)) return fail(LBM_EINVAL, "minority must be in [0, 1)");
+    if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
+    if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny - 2) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny - 2");
+    if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_TWO_PASS) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
+    if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
+    const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
+                           p->g, p->gx, p->amp, p->width, p->minority, p->y0, p->shift_A, p->shift_B};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(LBM_EINVAL, "parameters must be finite");
+    return LBM_OK;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* ws = nullptr;
+    bool own_ws = false;
+    Layout L;
+    lbm::Grid grid;
+    lbm::Physics phys;
+    float shift[2];
+    int cur = 0;
+    int64_t step = 0;
+    bool unstable = false;
+    double* host_out = nullptr;   // pinned, kDiagTerms + ny doubles
+    std::vector<double> last_rows;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    void* pops(int k) { return ws + L.pops[k]; }
+    double* scratch() { return (double*)(ws + L.scratch); }
+    int* flag() { return (int*)(ws + L.flag); }
+};
+
+namespace {
+
+lbm::StepLaunch step_launch(lbm_handle* h, int from) {
+    lbm::StepLaunch S;
+    S.fin = h->pops(from);
+    S.fout = h->pops(from ^ 1);
+    S.psi = (float*)(h->ws + h->L.psi);
+    S.flag = h->flag();
+    S.grid = h->grid;
+    S.phys = h->phys;
+    S.storage = h->p.storage;
+    S.tile_y = h->p.tile_y;
+    return S;
+}
+
+lbm::DiagLaunch diag_launch(lbm_handle* h) {
+    const lbm_params& p = h->p;
+    lbm::DiagLaunch D;
+    D.fin = h->pops(h->cur);
+    D.grid = h->grid;
+    D.storage = p.storage;
+    D.shift[0] = h->shift[0];
+    D.shift[1] = h->shift[1];
+    D.G = p.G;
+    D.G_wall[0] = p.G_wall_A;
+    D.G_wall[1] = p.G_wall_B;
+    D.g_ext[0] = -p.g;
+    D.g_ext[1] = p.gravity_mode == 0 ? p.g : -p.g;
+    D.gx = p.gx;
+    D.tau_bar = 0.5 * (p.tau_A + p.tau_B);
+    D.crop = p.crop_rows;
+    D.scratch = h->scratch();
+    D.partials = (double*)(h->ws + h->L.partials);
+    D.out = (double*)(h->ws + h->L.out);
+    return D;
+}
+
+void destroy_graphs(lbm_handle* h) {
+    for (auto& g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+lbm_status run_init(lbm_handle* h) {
+    std::vector<double> y0 = interface_height(h->p);
+    double* dy0 = (double*)(h->ws + h->L.y0);
+    LBM_TRY(cudaMemcpyAsync(dy0, y0.data(), y0.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy y0");
+    LBM_TRY(cudaMemsetAsync(h->flag(), 0, 16, h->stream), "clear flag");
+    LBM_TRY(lbm::launch_init(h->pops(0), h->grid, h->p.storage, h->shift, dy0, h->p.mass_A, h->p.mass_B,
+                             h->p.minority, h->p.width, h->stream), "init kernel");
+    // the copy reads y0 from pageable host memory: finish before the vector dies
+    LBM_TRY(cudaStreamSynchronize(h->stream), "init sync");
+    h->cur = 0;
+    h->step = 0;
+    h->unstable = false;
+    return LBM_OK;
+}
+
+lbm_status check_flag(lbm_handle* h) {
+    int flag = 0;
+    LBM_TRY(cudaMemcpyAsync(&flag, h->flag(), sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flag");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    if (flag) h->unstable = true;
+    return h->unstable ? fail(LBM_EUNSTABLE, "NaN or negative density seen by the step") : LBM_OK;
+}
+
+lbm_status launch_steps(lbm_handle* h, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        LBM_TRY(lbm::launch_step(step_launch(h, h->cur), h->p.kernel, h->stream), "step kernel");
+        h->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status get_graph(lbm_handle* h, int parity, cudaGraphExec_t* out) {
+    if (h->graph[parity]) {
+        *out = h->graph[parity];
+        return LBM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    LBM_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int cur = parity;
+    for (int k = 0; k < kGraphChunk; ++k) {
+        cudaError_t e = lbm::launch_step(step_launch(h, cur), h->p.kernel, h->stream);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e, "capture step");
+        }
+        cur ^= 1;
+    }
+    LBM_TRY(cudaStreamEndCapture(h->stream, &g), "end capture");
+    cudaError_t e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+    *out = h->graph[parity];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
+
+const char* lbm_status_str(lbm_status st) {
+    switch (st) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ENOMEM: return "out of memory";
+        case LBM_ECUDA: return "CUDA error";
+        case LBM_EUNSTABLE: return "unstable (NaN or negative density)";
+        case LBM_ETIMEOUT: return "device wait timed out";
+        case LBM_ESTATE: return "invalid state";
+        case LBM_EIO: return "I/O error";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_status lbm_params_default(lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->nx = 128;
+    p->ny = 256;
+    p->tau_A = p->tau_B = 1.0;
+    p->G = 1.4;
+    p->mass_A = 1.0;
+    p->mass_B = 0.9;
+    p->g = 1e-5;
+    p->gravity_mode = 0;
+    p->seed = 1;
+    p->n_modes = 8;
+    p->amp = 2.0;
+    p->width = 1.5;
+    p->minority = 0.08;
+    p->y0 = -1.0;
+    p->crop_rows = 10;
+    p->storage = LBM_STORE_F32;
+    p->kernel = LBM_KERNEL_FUSED;
+    p->tile_y = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_workspace_bytes(const lbm_params* p, size_t* bytes) {
+    lbm_status st = validate(p);
+    if (st != LBM_OK) return st;
+    if (!bytes) return fail(LBM_EINVAL, "bytes is NULL");
+    *bytes = make_layout(*p).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_bytes, void* cuda_stream,
+                         lbm_handle** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_status st = validate(p);
+    if (st != LBM_OK) return st;
+    Layout L = make_layout(*p);
+    if (dev_workspace && ws_bytes < L.total) return fail(LBM_ENOMEM, "workspace smaller than lbm_workspace_bytes");
+    if (dev_workspace && ((uintptr_t)dev_workspace % kAlign) != 0) return fail(LBM_EINVAL, "workspace must be 256-byte aligned");
+    lbm_handle* h = new lbm_handle();
+    h->p = *p;
+    h->L = L;
+    cudaGetDevice(&h->device);
+    if (dev_workspace) {
+        h->ws = (char*)dev_workspace;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&h->ws, L.total);
+        if (e != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+        }
+        h->own_ws = true;
+    }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            lbm_destroy(h);
+            return cuda_fail(e, "create stream");
+        }
+        h->own_stream = true;
+    }
+    cudaError_t e = cudaMallocHost((void**)&h->host_out, (lbm::kDiagTerms + (size_t)p->ny) * sizeof(double));
+    if (e != cudaSuccess) {
+        h->host_out = nullptr;
+        lbm_destroy(h);
+        return cuda_fail(e, "pinned host buffer");
+    }
+    // work queued on other streams (e.g. whoever produced the workspace) is done
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        lbm_destroy(h);
+        return cuda_fail(e, "synchronize");
+    }
+    h->grid.nx = p->nx;
+    h->grid.ny = p->ny;
+    h->grid.pitch = L.pitch;
+    h->grid.plane = L.plane;
+    const bool shifted = p->storage != LBM_STORE_F32;
+    const double sA = p->shift_A > 0.0 ? p->shift_A : 0.5 * p->mass_A * (1.0 + p->minority);
+    const double sB = p->shift_B > 0.0 ? p->shift_B : 0.5 * p->mass_B * (1.0 + p->minority);
+    h->shift[0] = shifted ? (float)sA : 0.0f;
+    h->shift[1] = shifted ? (float)sB : 0.0f;
+    lbm::Physics& ph = h->phys;
+    ph.tau[0] = (float)p->tau_A;
+    ph.tau[1] = (float)p->tau_B;
+    ph.om[0] = (float)(1.0 / p->tau_A);
+    ph.om[1] = (float)(1.0 / p->tau_B);
+    ph.G = (float)p->G;
+    // wall force: sum_i w_i S(x + c_i) c_i = (0, -1/6) on row 0 and (0, +1/6) on row ny-1
+    ph.ay_wall_bottom[0] = (float)(p->G_wall_A / 6.0);
+    ph.ay_wall_bottom[1] = (float)(p->G_wall_B / 6.0);
+    ph.ay_wall_top[0] = (float)(-p->G_wall_A / 6.0);
+    ph.ay_wall_top[1] = (float)(-p->G_wall_B / 6.0);
+    ph.ay_ext[0] = (float)(-p->g);
+    ph.ay_ext[1] = (float)(p->gravity_mode == 0 ? p->g : -p->g);
+    ph.ax_ext = (float)p->gx;
+    ph.shift[0] = h->shift[0];
+    ph.shift[1] = h->shift[1];
+    st = run_init(h);
+    if (st != LBM_OK) {
+        std::string msg = g_last_error;
+        lbm_destroy(h);
+        return fail(st, msg);
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(int32_t nx, int32_t ny, double tau, double G, double mass_A, double mass_B, double g,
+                      uint64_t seed, lbm_handle** out) {
+    lbm_params p;
+    lbm_params_default(&p);
+    p.nx = nx;
+    p.ny = ny;
+    p.tau_A = p.tau_B = tau;
+    p.G = G;
+    p.mass_A = mass_A;
+    p.mass_B = mass_B;
+    p.g = g;
+    p.seed = seed;
+    return lbm_create_ex(&p, nullptr, 0, nullptr, out);
+}
+
+lbm_status lbm_reset(lbm_handle* h) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    return run_init(h);
+}
+
+lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    if (h->unstable) return fail(LBM_EUNSTABLE, "state is unstable");
+    int64_t left = nsteps;
+    while (left >= kGraphChunk) {
+        cudaGraphExec_t g = nullptr;
+        lbm_status st = get_graph(h, h->cur, &g);
+        if (st != LBM_OK) return st;
+        LBM_TRY(cudaGraphLaunch(g, h->stream), "graph launch");
+        h->cur ^= (kGraphChunk & 1);
+        h->step += kGraphChunk;
+        left -= kGraphChunk;
+    }
+    lbm_status st = launch_steps(h, left);
+    if (st != LBM_OK) return st;
+    h->step += left;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_handle* h) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    return check_flag(h);
+}
+
+lbm_status lbm_step_count(lbm_handle* h, int64_t* step) {
+    if (!h || !step) return fail(LBM_EINVAL, "NULL argument");
+    *step = h->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
+    if (!h || !out) return fail(LBM_EINVAL, "NULL argument");
+    const lbm_params& p = h->p;
+    lbm::DiagLaunch D = diag_launch(h);
+    LBM_TRY(lbm::launch_diagnostics(D, h->stream), "diagnostics kernels");
+    const int nrows = p.ny - 2 * p.crop_rows;
+    LBM_TRY(cudaMemcpyAsync(h->host_out, D.out, (lbm::kDiagTerms + (size_t)nrows) * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream), "copy diagnostics");
+    lbm_status st = check_flag(h);  // synchronises the stream
+    if (st != LBM_OK && st != LBM_EUNSTABLE) return st;
+    const double* o = h->host_out;
+    const double Dn = (double)p.nx * nrows;
+    const double cs2 = 1.0 / 3.0;
+    const double tau_bar = 0.5 * (p.tau_A + p.tau_B);
+    std::memset(out, 0, sizeof(*out));
+    out->step = h->step;
+    out->mass_A = o[lbm::T_MASS_A];
+    out->mass_B = o[lbm::T_MASS_B];
+    out->E_k = o[lbm::T_EK] / Dn;
+    out->E_p = p.g * o[lbm::T_EP] / Dn;
+    out->buoyancy = p.g * o[lbm::T_BUOY] / Dn;
+    out->flux_pb = o[lbm::T_FLUX_PB] / Dn;
+    out->flux_K = o[lbm::T_FLUX_K] / Dn;
+    out->flux_tau = o[lbm::T_FLUX_TAU] / Dn;
+    out->rho_bar = o[lbm::T_RHO] / Dn;
+    const double eta = out->rho_bar * cs2 * (tau_bar - 0.5);
+    out->viscous = eta * o[lbm::T_VISC] / Dn;
+    out->enstrophy = 0.5 * o[lbm::T_OMEGA2];
+    for (int k = 0; k < 4; ++k) out->cc[k] = (int64_t)std::llround(o[lbm::T_N0 + k]);
+    out->L_int = (M_PI / 8.0) * ((double)out->cc[0] + (double)out->cc[1] +
+                                 ((double)out->cc[2] + (double)out->cc[3]) / std::sqrt(2.0));
+    // mixing-layer width from the normalised row means of phi
+    const double top = p.mass_A - p.minority * p.mass_B;
+    const double bot = p.minority * p.mass_A - p.mass_B;
+    h->last_rows.assign(nrows, 0.0);
+    double hw = 0.0;
+    for (int r = 0; r < nrows; ++r) {
+        const double mean = o[lbm::kDiagTerms + r] / p.nx;
+        h->last_rows[r] = mean;
+        double c = (mean - bot) / (top - bot);
+        c = c < 0.0 ? 0.0 : (c > 1.0 ? 1.0 : c);
+        hw += c * (1.0 - c);
+    }
+    out->h = 6.0 * hw;
+    out->status = h->unstable ? LBM_EUNSTABLE : LBM_OK;
+    return st;
+}
+
+lbm_status lbm_profile(lbm_handle* h, double* host_rows) {
+    if (!h || !host_rows) return fail(LBM_EINVAL, "NULL argument");
+    if (h->last_rows.empty()) return fail(LBM_ESTATE, "no diagnostics computed yet");
+    std::memcpy(host_rows, h->last_rows.data(), h->last_rows.size() * sizeof(double));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_handle* h, double* rhoA, double* rhoB, double* ux, double* uy) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    lbm::DiagLaunch D = diag_launch(h);
+    LBM_TRY(lbm::launch_fields(D, nullptr, h->stream), "fields kernels");
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    double* sc = h->scratch();
+    double* dst[4] = {rhoA, rhoB, ux, uy};
+    const size_t off[4] = {0, n, 4 * n, 5 * n};   // M[0], M[1], U[0], U[1]
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) LBM_TRY(cudaMemcpyAsync(dst[k], sc + off[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy fields");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_handle* h, double* host) {
+    if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+    double* S = h->scratch();
+    LBM_TRY(lbm::launch_pull_to_double(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream), "pull kernel");
+    const size_t n = (size_t)18 * h->p.nx * h->p.ny;
+    LBM_TRY(cudaMemcpyAsync(host, S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy populations");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle* h, const double* host) {
+    if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+    double* S = h->scratch();
+    const size_t n = (size_t)18 * h->p.nx * h->p.ny;
+    LBM_TRY(cudaMemcpyAsync(S, host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy populations");
+    LBM_TRY(lbm::launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream), "push kernel");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+struct SaveHeader {
+    char magic[8];
+    int32_t version, nx, ny, storage, pitch, cur;
+    int64_t step;
+    uint64_t bytes;
+    lbm_params params;
+};
+
+lbm_status lbm_save(lbm_handle* h, const char* path) {
+    if (!h || !path) return fail(LBM_EINVAL, "NULL argument");
+    std::vector<char> buf(h->L.pop_bytes);
+    LBM_TRY(cudaMemcpyAsync(buf.data(), h->pops(h->cur), buf.size(), cudaMemcpyDeviceToHost, h->stream), "copy state");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    SaveHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LBMSTAT1", 8);
+    hd.version = 1;
+    hd.nx = h->p.nx;
+    hd.ny = h->p.ny;
+    hd.storage = h->p.storage;
+    hd.pitch = h->L.pitch;
+    hd.step = h->step;
+    hd.bytes = buf.size();
+    hd.params = h->p;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(LBM_EIO, std::string("cannot open ") + path);
+    const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) return fail(LBM_EIO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_handle* h, const char* path) {
+    if (!h || !path) return fail(LBM_EINVAL, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(LBM_EIO, std::string("cannot open ") + path);
+    SaveHeader hd;
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "LBMSTAT1", 8) != 0) {
+        std::fclose(f);
+        return fail(LBM_EIO, "not a state file");
+    }
+    if (hd.nx != h->p.nx || hd.ny != h->p.ny || hd.storage != h->p.storage || hd.pitch != h->L.pitch ||
+        hd.bytes != h->L.pop_bytes) {
+        std::fclose(f);
+        return fail(LBM_EINVAL, "state file does not match the handle (nx, ny, storage)");
+    }
+    std::vector<char> buf(hd.bytes);
+    const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(LBM_EIO, "truncated state file");
+    LBM_TRY(cudaMemcpyAsync(h->pops(h->cur), buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream), "copy state");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    h->step = hd.step;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    if (h->host_out) cudaFreeHost(h->host_out);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

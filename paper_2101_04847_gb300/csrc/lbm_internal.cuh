@@ -1,0 +1,103 @@
+// Internal declarations shared by the CUDA translation units of liblbm.
+// Not part of the public ABI (include/lbm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice (Section 2): c_i, weights from the isotropy conditions,
+// opposite directions.  Direction order matches include/lbm.h.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 5 + 2) & 3) + 5);
+}
+__host__ __device__ constexpr float wf(int i) {
+    return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr double wd(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+constexpr int kThreadsX = 128;  // columns per block of the step kernels
+
+// Physical constants of one solver, in the form the kernels use.
+struct Physics {
+    float om[2];       // 1 / tau_s
+    float tau[2];      // tau_s
+    float G;           // G_AB
+    float ay_wall_bottom[2];  // wall-force acceleration on row 0 (per component)
+    float ay_wall_top[2];     // wall-force acceleration on row ny-1
+    float ay_ext[2];   // buoyancy acceleration along y (per component)
+    float ax_ext;      // body acceleration along x
+    float shift[2];    // rho0_s of the shifted storage (0 for FP32)
+};
+
+// Geometry of one population array set.
+struct Grid {
+    int nx, ny;
+    int pitch;          // elements per stored row (>= nx, multiple of 64)
+    size_t plane;       // elements per (component, direction) plane = ny * pitch
+};
+
+struct StepLaunch {
+    const void* fin;
+    void* fout;
+    float* psi;          // two-pass only: [2][ny][pitch]
+    int* flag;           // guard flag (NaN / negative density)
+    Grid grid;
+    Physics phys;
+    int storage;         // lbm_storage
+    int tile_y;
+};
+
+// step kernels (step_kernels.cu)
+cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st);
+cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shift[2],
+                        const double* y0, double mass_A, double mass_B, double minority,
+                        double width, cudaStream_t st);
+// S (double, [2][9][ny][nx]) from the stored state
+cudaError_t launch_pull_to_double(const void* fin, const Grid& g, int storage,
+                                  const float shift[2], double* S, cudaStream_t st);
+// stored state from S (double, [2][9][ny][nx])
+cudaError_t launch_push_from_double(const double* S, const Grid& g, int storage,
+                                    const float shift[2], void* fout, cudaStream_t st);
+
+// diagnostics (diag_kernels.cu)
+constexpr int kDiagTerms = 15;
+enum DiagTerm {
+    T_MASS_A = 0, T_MASS_B, T_EK, T_EP, T_BUOY, T_RHO, T_FLUX_PB, T_OMEGA2,
+    T_FLUX_K, T_FLUX_TAU, T_VISC, T_N0, T_N90, T_N45, T_N135
+};
+struct DiagLaunch {
+    const void* fin;
+    Grid grid;
+    int storage;
+    float shift[2];
+    double G, G_wall[2], g_ext[2], gx, tau_bar;
+    int crop;
+    double* scratch;     // 15 doubles per site
+    double* partials;    // kDiagTerms * nblocks + ny * nbx
+    double* out;         // kDiagTerms + ny doubles
+};
+size_t diag_scratch_doubles(int nx, int ny);
+size_t diag_partials_doubles(int nx, int ny);
+cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st);
+// rho_A, rho_B, ux, uy (double [ny][nx] each) into `fields` (4 * nx * ny doubles);
+// uses scratch (15 doubles per site)
+cudaError_t launch_fields(const DiagLaunch& D, double* fields, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,370 @@
+// Time-step kernels of the two-component D2Q9 Shan-Chen solver (Section 2 of
+// arXiv 2101.04847): pull streaming with periodic x and half-way bounce-back
+// walls, densities and common velocity (Eq. 1), Shan-Chen + wall + buoyancy
+// accelerations, forced BGK collision with the shifted-velocity equilibrium.
+//
+// Storage convention.  A buffer B holds *post-collision* populations; the
+// post-streaming populations of the kinetic equation are obtained by pulling:
+//     S_i(x, y) = B_i(x - c_ix, y - c_iy)   if 0 <= y - c_iy < ny
+//     S_i(x, y) = B_opp(i)(x, y)            otherwise (bounce-back at the wall)
+// Layout: structure of arrays [component][direction][y][pitch], x fastest.
+#include "lattice.cuh"
+
+namespace lbm {
+
+// Neighbour sums of the pseudopotential of one component:
+// (nx, ny) = sum_i w_i psi(x + c_i) c_i.
+struct Nbr { float E, W, N, S, NE, NW, SE, SW; };
+__device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
+    sx = (1.0f / 9.0f) * (r.E - r.W) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.SE - r.NW));
+    sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
+}
+
+// Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
+// "Equilibrium distribution"): f <- f + (f^eq(rho_s, u + tau_s a_s) - f) / tau_s with
+// a_s = F_s / rho_s computed directly (no division by rho_s).
+__device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, const Nbr& psiB,
+                                             const Physics& ph, int y, int ny, int* flag) {
+    const float rA = sum9(f[0]);
+    const float rB = sum9(f[1]);
+    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) *flag = 1;
+    float jx[2], jy[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]);
+        jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]);
+    }
+    const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
+    const float ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
+    const float uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;
+    float nAx, nAy, nBx, nBy;
+    nbr_sum(psiA, nAx, nAy);
+    nbr_sum(psiB, nBx, nBy);
+    float ax[2], ay[2];
+    ax[0] = -ph.G * nBx + ph.ax_ext;
+    ay[0] = -ph.G * nBy + ph.ay_ext[0];
+    ax[1] = -ph.G * nAx + ph.ax_ext;
+    ay[1] = -ph.G * nAy + ph.ay_ext[1];
+    if (y == 0) { ay[0] += ph.ay_wall_bottom[0]; ay[1] += ph.ay_wall_bottom[1]; }
+    if (y == ny - 1) { ay[0] += ph.ay_wall_top[0]; ay[1] += ph.ay_wall_top[1]; }
+    const float rho[2] = {rA, rB};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float vx = ux + ph.tau[s] * ax[s];
+        const float vy = uy + ph.tau[s] * ay[s];
+        const float usq = 1.5f * (vx * vx + vy * vy);
+        const float om = ph.om[s];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float cu = (float)cx(i) * vx + (float)cy(i) * vy;
+            const float feq = rho[s] * wf(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq);
+            f[s][i] = f[s][i] + om * (feq - f[s][i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused pull stream-collide.  A block owns kThreadsX columns and tile_y rows and
+// sweeps its rows bottom-up.  Each thread keeps the populations of its column for
+// the current and the next row in registers; the densities of three consecutive
+// rows (plus one halo column each side) live in a 4-slot shared-memory ring.
+// The only redundant loads are the pulls of the halo columns and of the two halo
+// rows y0 - 1 and y1, which only feed densities.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX)
+step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+    __shared__ float sR[4][2][kThreadsX + 2];
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * kThreadsX;
+    const int w = min(kThreadsX, g.nx - x0);
+    const int y0 = blockIdx.y * tile_y;
+    const int y1 = min(y0 + tile_y, g.ny);
+    const bool active = t < w;
+    const int x = x0 + (active ? t : w - 1);
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    // halo columns: left one pulled by thread 0, right one by thread max(w-1, 1)
+    const bool haloL = (t == 0);
+    const bool haloR = (t == max(w - 1, 1));
+    const int hx = haloL ? (x0 == 0 ? g.nx - 1 : x0 - 1) : ((x0 + w) % g.nx);
+    const int hxm = hx == 0 ? g.nx - 1 : hx - 1;
+    const int hxp = hx == g.nx - 1 ? 0 : hx + 1;
+    const int hk = haloL ? 0 : w + 1;
+    const bool halo = haloL || haloR;
+    const float shift[2] = {ph.shift[0], ph.shift[1]};
+
+    float cur[2][9];
+    // rows y0-1 (density only) and y0
+    {
+        const int slot = (y0 - 1) & 3;
+        float rA = 0.0f, rB = 0.0f, hA = 0.0f, hB = 0.0f;
+        if (y0 > 0) {
+            float tmp[2][9];
+            pull_site<T>(fin, g, shift, y0 - 1, x, xm, xp, tmp);
+            rA = sum9(tmp[0]); rB = sum9(tmp[1]);
+            if (halo) {
+                pull_site<T>(fin, g, shift, y0 - 1, hx, hxm, hxp, tmp);
+                hA = sum9(tmp[0]); hB = sum9(tmp[1]);
+            }
+        }
+        if (active) { sR[slot][0][t + 1] = rA; sR[slot][1][t + 1] = rB; }
+        if (halo) { sR[slot][0][hk] = hA; sR[slot][1][hk] = hB; }
+    }
+    {
+        const int slot = y0 & 3;
+        pull_site<T>(fin, g, shift, y0, x, xm, xp, cur);
+        if (active) { sR[slot][0][t + 1] = sum9(cur[0]); sR[slot][1][t + 1] = sum9(cur[1]); }
+        if (halo) {
+            float tmp[2][9];
+            pull_site<T>(fin, g, shift, y0, hx, hxm, hxp, tmp);
+            sR[slot][0][hk] = sum9(tmp[0]); sR[slot][1][hk] = sum9(tmp[1]);
+        }
+    }
+    for (int y = y0; y < y1; ++y) {
+        float nxt[2][9];
+        const int sn = (y + 1) & 3;
+        if (y + 1 < g.ny) {
+            pull_site<T>(fin, g, shift, y + 1, x, xm, xp, nxt);
+            if (active) { sR[sn][0][t + 1] = sum9(nxt[0]); sR[sn][1][t + 1] = sum9(nxt[1]); }
+            if (halo) {
+                float tmp[2][9];
+                pull_site<T>(fin, g, shift, y + 1, hx, hxm, hxp, tmp);
+                sR[sn][0][hk] = sum9(tmp[0]); sR[sn][1][hk] = sum9(tmp[1]);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) nxt[s][i] = 0.0f;
+            if (active) { sR[sn][0][t + 1] = 0.0f; sR[sn][1][t + 1] = 0.0f; }
+            if (halo) { sR[sn][0][hk] = 0.0f; sR[sn][1][hk] = 0.0f; }
+        }
+        __syncthreads();
+        if (active) {
+            const int k = t + 1;
+            const int s0 = (y - 1) & 3, s1 = y & 3, s2 = sn;
+            Nbr pA, pB;
+            pA.E = sR[s1][0][k + 1]; pA.W = sR[s1][0][k - 1];
+            pA.N = sR[s2][0][k];     pA.S = sR[s0][0][k];
+            pA.NE = sR[s2][0][k + 1]; pA.NW = sR[s2][0][k - 1];
+            pA.SE = sR[s0][0][k + 1]; pA.SW = sR[s0][0][k - 1];
+            pB.E = sR[s1][1][k + 1]; pB.W = sR[s1][1][k - 1];
+            pB.N = sR[s2][1][k];     pB.S = sR[s0][1][k];
+            pB.NE = sR[s2][1][k + 1]; pB.NW = sR[s2][1][k - 1];
+            pB.SE = sR[s0][1][k + 1]; pB.SW = sR[s0][1][k - 1];
+            collide_site(cur, pA, pB, ph, y, g.ny, flag);
+            const size_t row = (size_t)y * g.pitch + x;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + row, i, cur[s][i], shift[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) cur[s][i] = nxt[s][i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass step: densities into psi, then pull + collide reading psi neighbours.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX)
+density_kernel(const T* __restrict__ fin, float* __restrict__ psi, Grid g, Physics ph) {
+    const int x = blockIdx.x * kThreadsX + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9];
+    pull_site<T>(fin, g, ph.shift, y, x, xm, xp, f);
+    psi[(size_t)y * g.pitch + x] = sum9(f[0]);
+    psi[g.plane + (size_t)y * g.pitch + x] = sum9(f[1]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX)
+collide_kernel(const T* __restrict__ fin, const float* __restrict__ psi, T* __restrict__ fout,
+               Grid g, Physics ph, int* flag) {
+    const int x = blockIdx.x * kThreadsX + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9];
+    pull_site<T>(fin, g, ph.shift, y, x, xm, xp, f);
+    Nbr p[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float* q = psi + (size_t)s * g.plane;
+        const float* r0 = q + (size_t)y * g.pitch;
+        p[s].E = __ldg(r0 + xp);
+        p[s].W = __ldg(r0 + xm);
+        if (y + 1 < g.ny) {
+            const float* r = q + (size_t)(y + 1) * g.pitch;
+            p[s].N = __ldg(r + x); p[s].NE = __ldg(r + xp); p[s].NW = __ldg(r + xm);
+        } else {
+            p[s].N = p[s].NE = p[s].NW = 0.0f;
+        }
+        if (y > 0) {
+            const float* r = q + (size_t)(y - 1) * g.pitch;
+            p[s].S = __ldg(r + x); p[s].SE = __ldg(r + xp); p[s].SW = __ldg(r + xm);
+        } else {
+            p[s].S = p[s].SE = p[s].SW = 0.0f;
+        }
+    }
+    collide_site(f, p[0], p[1], ph, y, g.ny, flag);
+    const size_t row = (size_t)y * g.pitch + x;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + row, i, f[s][i], ph.shift[s]);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (Section 2, last paragraph): densities of a tanh interface at
+// height y0(x), fluid at rest, f = w_i rho_s; stored as the buffer whose pull
+// gives those populations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void init_rho(const double* y0, int x, int y, double mA, double mB,
+                                         double eps, double width, double& rA, double& rB) {
+    const double H = 0.5 * (1.0 + tanh(((double)y - y0[x]) / width));
+    rA = mA * (eps + (1.0 - eps) * H);
+    rB = mB * (eps + (1.0 - eps) * (1.0 - H));
+}
+
+template <typename T>
+__global__ void init_kernel(T* __restrict__ fout, Grid g, float sA, float sB, const double* __restrict__ y0,
+                            double mA, double mB, double eps, double width) {
+    const int x = blockIdx.x * kThreadsX + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const float shift[2] = {sA, sB};
+    double here[2];
+    init_rho(y0, x, y, mA, mB, eps, width, here[0], here[1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ty = y + cy(i);
+        const int tx = (x + cx(i) + g.nx) % g.nx;
+        double r[2] = {here[0], here[1]};
+        if (ty >= 0 && ty < g.ny) init_rho(y0, tx, ty, mA, mB, eps, width, r[0], r[1]);
+        for (int s = 0; s < 2; ++s)
+            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + (size_t)y * g.pitch + x, i,
+                         (float)(wd(i) * r[s]), shift[s]);
+    }
+}
+
+template <typename T>
+__global__ void pull_to_double_kernel(const T* __restrict__ fin, Grid g, float sA, float sB, double* __restrict__ S) {
+    const int x = blockIdx.x * kThreadsX + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const float shift[2] = {sA, sB};
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9];
+    pull_site<T>(fin, g, shift, y, x, xm, xp, f);
+    const size_t n = (size_t)g.nx * g.ny;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 9; ++i) S[(size_t)(s * 9 + i) * n + (size_t)y * g.nx + x] = (double)f[s][i];
+}
+
+template <typename T>
+__global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, float sA, float sB, T* __restrict__ fout) {
+    const int x = blockIdx.x * kThreadsX + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const float shift[2] = {sA, sB};
+    const size_t n = (size_t)g.nx * g.ny;
+    for (int s = 0; s < 2; ++s) {
+        for (int i = 0; i < 9; ++i) {
+            const int ty = y + cy(i);
+            const int tx = (x + cx(i) + g.nx) % g.nx;
+            const double v = (ty >= 0 && ty < g.ny)
+                ? S[(size_t)(s * 9 + i) * n + (size_t)ty * g.nx + tx]
+                : S[(size_t)(s * 9 + opp(i)) * n + (size_t)y * g.nx + x];
+            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + (size_t)y * g.pitch + x, i, (float)v, shift[s]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t st) {
+    const Grid& g = L.grid;
+    const int bx = (g.nx + kThreadsX - 1) / kThreadsX;
+    if (kernel == LBM_KERNEL_TWO_PASS) {
+        dim3 grid(bx, g.ny);
+        density_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, g, L.phys);
+        collide_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, (T*)L.fout, g, L.phys, L.flag);
+    } else {
+        const int ty = L.tile_y > 0 ? L.tile_y : 16;
+        dim3 grid(bx, (g.ny + ty - 1) / ty);
+        step_fused_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st) {
+    switch (L.storage) {
+        case LBM_STORE_F16: return launch_step_t<__half>(L, kernel, st);
+        case LBM_STORE_BF16: return launch_step_t<__nv_bfloat16>(L, kernel, st);
+        default: return launch_step_t<float>(L, kernel, st);
+    }
+}
+
+cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shift[2], const double* y0,
+                        double mass_A, double mass_B, double minority, double width, cudaStream_t st) {
+    dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
+    switch (storage) {
+        case LBM_STORE_F16:
+            init_kernel<__half><<<grid, kThreadsX, 0, st>>>((__half*)fout, g, shift[0], shift[1], y0, mass_A, mass_B, minority, width);
+            break;
+        case LBM_STORE_BF16:
+            init_kernel<__nv_bfloat16><<<grid, kThreadsX, 0, st>>>((__nv_bfloat16*)fout, g, shift[0], shift[1], y0, mass_A, mass_B, minority, width);
+            break;
+        default:
+            init_kernel<float><<<grid, kThreadsX, 0, st>>>((float*)fout, g, shift[0], shift[1], y0, mass_A, mass_B, minority, width);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull_to_double(const void* fin, const Grid& g, int storage, const float shift[2], double* S,
+                                  cudaStream_t st) {
+    dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
+    switch (storage) {
+        case LBM_STORE_F16:
+            pull_to_double_kernel<__half><<<grid, kThreadsX, 0, st>>>((const __half*)fin, g, shift[0], shift[1], S);
+            break;
+        case LBM_STORE_BF16:
+            pull_to_double_kernel<__nv_bfloat16><<<grid, kThreadsX, 0, st>>>((const __nv_bfloat16*)fin, g, shift[0], shift[1], S);
+            break;
+        default:
+            pull_to_double_kernel<float><<<grid, kThreadsX, 0, st>>>((const float*)fin, g, shift[0], shift[1], S);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_from_double(const double* S, const Grid& g, int storage, const float shift[2], void* fout,
+                                    cudaStream_t st) {
+    dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
+    switch (storage) {
+        case LBM_STORE_F16:
+            push_from_double_kernel<__half><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (__half*)fout);
+            break;
+        case LBM_STORE_BF16:
+            push_from_double_kernel<__nv_bfloat16><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (__nv_bfloat16*)fout);
+            break;
+        default:
+            push_from_double_kernel<float><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (float*)fout);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

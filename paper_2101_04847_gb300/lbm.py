@@ -1,0 +1,239 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels of
+the library.  PyTorch supplies device memory (the workspace) and the stream.
+If the library has not been built, importing works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+KERNEL = {"fused": 0, "two_pass": 1}
+
+
+class LbmParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("tau_A", C.c_double), ("tau_B", C.c_double),
+        ("G", C.c_double), ("G_wall_A", C.c_double), ("G_wall_B", C.c_double),
+        ("mass_A", C.c_double), ("mass_B", C.c_double),
+        ("g", C.c_double), ("gravity_mode", C.c_int32), ("gx", C.c_double),
+        ("seed", C.c_uint64), ("n_modes", C.c_int32),
+        ("amp", C.c_double), ("width", C.c_double), ("minority", C.c_double), ("y0", C.c_double),
+        ("crop_rows", C.c_int32), ("storage", C.c_int32), ("kernel", C.c_int32), ("tile_y", C.c_int32),
+        ("shift_A", C.c_double), ("shift_B", C.c_double),
+    ]
+
+
+class LbmDiag(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64),
+        ("mass_A", C.c_double), ("mass_B", C.c_double),
+        ("E_k", C.c_double), ("E_p", C.c_double), ("buoyancy", C.c_double),
+        ("flux_pb", C.c_double), ("flux_K", C.c_double), ("flux_tau", C.c_double),
+        ("viscous", C.c_double), ("enstrophy", C.c_double), ("rho_bar", C.c_double),
+        ("h", C.c_double), ("L_int", C.c_double),
+        ("cc", C.c_int64 * 4), ("status", C.c_int32),
+    ]
+
+
+_P = C.POINTER
+_dp = _P(C.c_double)
+_h = C.c_void_p
+_PROTOS = {
+    "lbm_version": (C.c_char_p, []),
+    "lbm_status_str": (C.c_char_p, [C.c_int]),
+    "lbm_last_error": (C.c_char_p, []),
+    "lbm_params_default": (C.c_int, [_P(LbmParams)]),
+    "lbm_workspace_bytes": (C.c_int, [_P(LbmParams), _P(C.c_size_t)]),
+    "lbm_create": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
+                             C.c_double, C.c_uint64, _P(_h)]),
+    "lbm_create_ex": (C.c_int, [_P(LbmParams), C.c_void_p, C.c_size_t, C.c_void_p, _P(_h)]),
+    "lbm_reset": (C.c_int, [_h]),
+    "lbm_step": (C.c_int, [_h, C.c_int64]),
+    "lbm_sync": (C.c_int, [_h]),
+    "lbm_step_count": (C.c_int, [_h, _P(C.c_int64)]),
+    "lbm_diagnostics": (C.c_int, [_h, _P(LbmDiag)]),
+    "lbm_profile": (C.c_int, [_h, _dp]),
+    "lbm_get_fields": (C.c_int, [_h, _dp, _dp, _dp, _dp]),
+    "lbm_get_populations": (C.c_int, [_h, _dp]),
+    "lbm_set_populations": (C.c_int, [_h, _dp]),
+    "lbm_save": (C.c_int, [_h, C.c_char_p]),
+    "lbm_load": (C.c_int, [_h, C.c_char_p]),
+    "lbm_destroy": (None, [_h]),
+}
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+def load_library(path: str | Path | None = None) -> C.CDLL:
+    """Load liblbm.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path is not None else _LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"liblbm.so not found at {p}: run __graft_entry__.build() "
+                           "(python -c 'import __graft_entry__ as g; g.build()') first")
+    lib = C.CDLL(str(p))
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(st: int, where: str) -> int:
+    if st != LBM_OK:
+        lib = load_library()
+        raise LbmError(st, where, lib.lbm_last_error().decode() or lib.lbm_status_str(st).decode())
+    return st
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def default_params(**overrides) -> LbmParams:
+    p = LbmParams()
+    _check(load_library().lbm_params_default(C.byref(p)), "lbm_params_default")
+    for k, v in overrides.items():
+        if k == "storage" and isinstance(v, str):
+            v = STORAGE[v]
+        if k == "kernel" and isinstance(v, str):
+            v = KERNEL[v]
+        if not hasattr(p, k):
+            raise KeyError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def params_dict(p: LbmParams) -> dict:
+    return {name: getattr(p, name) for name, _ in LbmParams._fields_}
+
+
+def workspace_bytes(p: LbmParams) -> int:
+    n = C.c_size_t()
+    _check(load_library().lbm_workspace_bytes(C.byref(p), C.byref(n)), "lbm_workspace_bytes")
+    return n.value
+
+
+def diag_dict(d: LbmDiag) -> dict:
+    out = {name: getattr(d, name) for name, _ in LbmDiag._fields_ if name != "cc"}
+    out["cc"] = np.array(list(d.cc), dtype=np.int64)
+    return out
+
+
+class Solver:
+    """One solver instance on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor owned by this object; work runs
+    on the torch stream current at construction (or on a library stream when that
+    is the legacy default stream).
+    """
+
+    def __init__(self, params: LbmParams | None = None, **overrides):
+        import torch
+
+        lib = load_library()
+        self.lib = lib
+        self.params = params if params is not None else default_params(**overrides)
+        if params is not None and overrides:
+            for k, v in overrides.items():
+                setattr(self.params, k, v)
+        self.nx, self.ny = self.params.nx, self.params.ny
+        nbytes = workspace_bytes(self.params)
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream or None
+        self._h = C.c_void_p()
+        _check(lib.lbm_create_ex(C.byref(self.params), C.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 C.c_void_p(sp) if sp else None, C.byref(self._h)), "lbm_create_ex")
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.lbm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API -----------------------------------------------------------------
+    def reset(self):
+        _check(self.lib.lbm_reset(self._h), "lbm_reset")
+
+    def step(self, n: int = 1):
+        _check(self.lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    def sync(self):
+        _check(self.lib.lbm_sync(self._h), "lbm_sync")
+
+    @property
+    def step_count(self) -> int:
+        v = C.c_int64()
+        _check(self.lib.lbm_step_count(self._h, C.byref(v)), "lbm_step_count")
+        return v.value
+
+    def diagnostics(self, check: bool = True) -> dict:
+        d = LbmDiag()
+        st = self.lib.lbm_diagnostics(self._h, C.byref(d))
+        if check or st not in (LBM_OK, LBM_EUNSTABLE):
+            _check(st, "lbm_diagnostics")
+        return diag_dict(d)
+
+    def profile(self) -> np.ndarray:
+        rows = np.empty(self.ny - 2 * self.params.crop_rows)
+        _check(self.lib.lbm_profile(self._h, _ptr(rows)), "lbm_profile")
+        return rows
+
+    def fields(self) -> dict:
+        out = {k: np.empty((self.ny, self.nx)) for k in ("rhoA", "rhoB", "ux", "uy")}
+        _check(self.lib.lbm_get_fields(self._h, *(_ptr(out[k]) for k in ("rhoA", "rhoB", "ux", "uy"))),
+               "lbm_get_fields")
+        return out
+
+    def populations(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((2, 9, self.ny, self.nx))
+        _check(self.lib.lbm_get_populations(self._h, _ptr(out)), "lbm_get_populations")
+        return out
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (2, 9, self.ny, self.nx):
+            raise ValueError(f"populations must have shape (2, 9, {self.ny}, {self.nx})")
+        _check(self.lib.lbm_set_populations(self._h, _ptr(f)), "lbm_set_populations")
+
+    def save(self, path: str | Path):
+        _check(self.lib.lbm_save(self._h, str(path).encode()), "lbm_save")
+
+    def load(self, path: str | Path):
+        _check(self.lib.lbm_load(self._h, str(path).encode()), "lbm_load")

@@ -1,0 +1,110 @@
+"""Host API behaviour on the GPU: checkpoints, reset, the instability guard,
+library-owned memory, storage round trips."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2101_04847_gb300 import lbm
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_checkpoint_round_trip_is_bitwise(gpu, tmp_path):
+    d = inputs.params(inputs.C0, nx=160, ny=96)
+    path = tmp_path / "state.bin"
+    with lbm.Solver(**d) as a:
+        a.step(37)
+        a.save(path)
+        a.step(25)
+        want = a.populations()
+        with lbm.Solver(**d) as b:
+            b.load(path)
+            assert b.step_count == 37
+            b.step(25)
+            assert np.array_equal(b.populations(), want)
+
+
+def test_load_rejects_a_mismatched_grid(gpu, tmp_path):
+    path = tmp_path / "state.bin"
+    with lbm.Solver(**inputs.params(inputs.C0, nx=64, ny=64)) as a:
+        a.save(path)
+    with lbm.Solver(**inputs.params(inputs.C0, nx=64, ny=72)) as b:
+        with pytest.raises(lbm.LbmError) as e:
+            b.load(path)
+        assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_reset_restores_the_initial_state(gpu):
+    with lbm.Solver(**inputs.params(inputs.C0, nx=64, ny=64)) as s:
+        f0 = s.populations()
+        s.step(30)
+        s.reset()
+        assert s.step_count == 0
+        assert np.array_equal(s.populations(), f0)
+
+
+def test_nan_is_reported_as_unstable_and_is_sticky(gpu):
+    nx, ny = 64, 32
+    with lbm.Solver(**inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=4)) as s:
+        f = s.populations()
+        f[0, 0, 10, 10] = np.nan
+        s.set_populations(f)
+        s.step(3)
+        with pytest.raises(lbm.LbmError) as e:
+            s.sync()
+        assert e.value.status == lbm.LBM_EUNSTABLE
+        d = s.diagnostics(check=False)
+        assert d["status"] == lbm.LBM_EUNSTABLE
+        with pytest.raises(lbm.LbmError):
+            s.step(1)
+
+
+def test_negative_density_is_reported_as_unstable(gpu):
+    nx, ny = 64, 32
+    with lbm.Solver(**inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=4)) as s:
+        f = s.populations()
+        f[1, :, 5, 7] = -0.5
+        s.set_populations(f)
+        s.step(1)
+        with pytest.raises(lbm.LbmError) as e:
+            s.sync()
+        assert e.value.status == lbm.LBM_EUNSTABLE
+
+
+def test_library_owned_memory_and_stream(gpu):
+    lib = gpu
+    h = C.c_void_p()
+    assert lib.lbm_create(96, 64, 0.8, 1.2, 1.0, 1.0, 1e-5, 7, C.byref(h)) == lbm.LBM_OK
+    assert lib.lbm_step(h, 10) == lbm.LBM_OK
+    d = lbm.LbmDiag()
+    assert lib.lbm_diagnostics(h, C.byref(d)) == lbm.LBM_OK
+    assert d.step == 10 and d.mass_A > 0
+    lib.lbm_destroy(h)
+
+
+def test_workspace_too_small_is_rejected(gpu):
+    import torch
+
+    p = lbm.default_params(nx=64, ny=64)
+    n = lbm.workspace_bytes(p)
+    ws = torch.empty(n // 2, dtype=torch.uint8, device="cuda")
+    h = C.c_void_p()
+    st = gpu.lbm_create_ex(C.byref(p), C.c_void_p(ws.data_ptr()), n // 2, None, C.byref(h))
+    assert st == lbm.LBM_ENOMEM and not h.value
+
+
+def test_runs_on_a_caller_stream(gpu):
+    import torch
+
+    d = inputs.params(inputs.C0, nx=96, ny=64)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        a = lbm.Solver(**d)
+    b = lbm.Solver(**d)
+    a.step(60)
+    b.step(60)
+    assert np.array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
