@@ -51,7 +51,7 @@ typedef enum {
     LBM_ENOMEM = 2,     /* allocation failed or workspace too small */
     LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
     LBM_EUNSTABLE = 4,  /* sticky: a NaN or negative density was seen by the step */
-    LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LBM_ETIMEOUT = 5,   /* sticky: a bounded device-side wait gave up */
     LBM_ESTATE = 6,     /* call not valid in the handle's current state */
     LBM_EIO = 7         /* file I/O error (save/load) */
 } lbm_status;
@@ -63,8 +63,9 @@ typedef enum {
 } lbm_storage;
 
 typedef enum {
-    LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step */
-    LBM_KERNEL_TWO_PASS = 1  /* density kernel + stream-collide kernel per step */
+    LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step (global-memory pulls) */
+    LBM_KERNEL_TWO_PASS = 1, /* density kernel + stream-collide kernel per step */
+    LBM_KERNEL_STAGED = 2    /* fused kernel with rows staged in shared memory by bulk async copies */
 } lbm_kernel;
 
 /* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
@@ -84,7 +85,7 @@ typedef struct {
     double width;            /* tanh half-width of the initial interface, > 0 */
     double minority;         /* fraction of the other component in each bulk, [0, 1) */
     double y0;               /* mean interface height; < 0 means ny / 2 */
-    int32_t crop_rows;       /* rows cut at top and bottom for averages, >= 3, 2*crop_rows < ny - 2 */
+    int32_t crop_rows;       /* rows cut at top and bottom for averages, >= 3, 2*crop_rows < ny */
     int32_t storage;         /* lbm_storage */
     int32_t kernel;          /* lbm_kernel */
     int32_t tile_y;          /* rows per block of the fused kernel; 0 = default */

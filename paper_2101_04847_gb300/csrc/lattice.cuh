@@ -31,11 +31,6 @@ __device__ __forceinline__ float load_pop(const T* p, int i, float shift_s) {
     if (IsShifted<T>::value) v += wf(i) * shift_s;
     return v;
 }
-template <typename T>
-__device__ __forceinline__ void store_pop(T* p, int i, float v, float shift_s) {
-    if (IsShifted<T>::value) v -= wf(i) * shift_s;
-    *p = from_f<T>(v);
-}
 
 // Pull the 18 post-streaming populations of column xc (neighbours xm, xp) on row y.
 template <typename T>
@@ -49,9 +44,30 @@ __device__ __forceinline__ void pull_site(const T* __restrict__ fin, const Grid&
             const int sx = cx(i) == 0 ? xc : (cx(i) == 1 ? xm : xp);
             const bool inside = (cy(i) == 0) || (sy >= 0 && sy < g.ny);
             const size_t idx = inside
-                ? (size_t)(s * 9 + i) * g.plane + (size_t)sy * g.pitch + sx
-                : (size_t)(s * 9 + opp(i)) * g.plane + (size_t)y * g.pitch + xc;
+                ? (size_t)(s * 9 + i) * g.plane + (size_t)sy * g.pitch + g.origin + sx
+                : (size_t)(s * 9 + opp(i)) * g.plane + (size_t)y * g.pitch + g.origin + xc;
             f[s][i] = load_pop<T>(fin + idx, i, shift[s]);
+        }
+    }
+}
+
+// Store the 18 post-collision values of column x on row y, plus the periodic ghost
+// copy of the two first / last columns (read by the staged kernel's row windows).
+template <typename T>
+__device__ __forceinline__ void store_site(T* __restrict__ fout, const Grid& g, int y, int x,
+                                           const float f[2][9], const float shift[2]) {
+    const size_t row = (size_t)y * g.pitch + g.origin;
+    const int xg = x < 2 ? x + g.nx : (x >= g.nx - 2 ? x - g.nx : x);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float v = f[s][i];
+            if (IsShifted<T>::value) v -= wf(i) * shift[s];
+            const T tv = from_f<T>(v);
+            T* q = fout + (size_t)(s * 9 + i) * g.plane + row;
+            q[x] = tv;
+            if (xg != x) q[xg] = tv;
         }
     }
 }

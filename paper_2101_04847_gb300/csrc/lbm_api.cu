@@ -77,12 +77,15 @@ std::vector<double> interface_height(const lbm_params& p) {
 struct Layout {
     size_t pops[2], psi, scratch, partials, out, flag, y0, total;
     size_t pop_bytes, plane;
-    int pitch;
+    int pitch, origin;
 };
 
 Layout make_layout(const lbm_params& p) {
     Layout L;
-    L.pitch = (p.nx + 63) / 64 * 64;
+    // column 0 sits 128 bytes into each row; the row leaves room for the staged
+    // kernel's windows (columns -8 .. roundup(nx, 128) + 8) and the ghost copies
+    L.origin = (int)(128 / elem_size(p.storage));
+    L.pitch = (p.nx + lbm::kThreadsX - 1) / lbm::kThreadsX * lbm::kThreadsX + 2 * L.origin;
     L.plane = (size_t)p.ny * L.pitch;
     L.pop_bytes = 18 * L.plane * elem_size(p.storage);
     const size_t n = (size_t)p.nx * p.ny;
@@ -109,9 +112,9 @@ lbm_status validate(const lbm_params* p) {
     if (!(p->width > 0.0)) return fail(LBM_EINVAL, "width must be > 0");
     if (!(p->minority >= 0.0 && p->minority < 1.0)) return fail(LBM_EINVAL, "minority must be in [0, 1)");
     if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
-    if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny - 2) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny - 2");
+    if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny");
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
-    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_TWO_PASS) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_STAGED) return fail(LBM_EINVAL, "unknown kernel");
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
     const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
@@ -137,6 +140,7 @@ struct lbm_handle {
     int cur = 0;
     int64_t step = 0;
     bool unstable = false;
+    bool timed_out = false;
     double* host_out = nullptr;   // pinned, kDiagTerms + ny doubles
     std::vector<double> last_rows;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -195,6 +199,9 @@ lbm_status run_init(lbm_handle* h) {
     double* dy0 = (double*)(h->ws + h->L.y0);
     LBM_TRY(cudaMemcpyAsync(dy0, y0.data(), y0.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy y0");
     LBM_TRY(cudaMemsetAsync(h->flag(), 0, 16, h->stream), "clear flag");
+    // padding and unused window columns of both buffers start at zero
+    LBM_TRY(cudaMemsetAsync(h->pops(0), 0, h->L.pop_bytes, h->stream), "clear populations");
+    LBM_TRY(cudaMemsetAsync(h->pops(1), 0, h->L.pop_bytes, h->stream), "clear populations");
     LBM_TRY(lbm::launch_init(h->pops(0), h->grid, h->p.storage, h->shift, dy0, h->p.mass_A, h->p.mass_B,
                              h->p.minority, h->p.width, h->stream), "init kernel");
     // the copy reads y0 from pageable host memory: finish before the vector dies
@@ -202,6 +209,7 @@ lbm_status run_init(lbm_handle* h) {
     h->cur = 0;
     h->step = 0;
     h->unstable = false;
+    h->timed_out = false;
     return LBM_OK;
 }
 
@@ -209,7 +217,9 @@ lbm_status check_flag(lbm_handle* h) {
     int flag = 0;
     LBM_TRY(cudaMemcpyAsync(&flag, h->flag(), sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flag");
     LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
-    if (flag) h->unstable = true;
+    if (flag & 1) h->unstable = true;
+    if (flag & 2) h->timed_out = true;
+    if (h->timed_out) return fail(LBM_ETIMEOUT, "a bounded wait for a staged row copy gave up");
     return h->unstable ? fail(LBM_EUNSTABLE, "NaN or negative density seen by the step") : LBM_OK;
 }
 
@@ -349,6 +359,7 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     h->grid.nx = p->nx;
     h->grid.ny = p->ny;
     h->grid.pitch = L.pitch;
+    h->grid.origin = L.origin;
     h->grid.plane = L.plane;
     const bool shifted = p->storage != LBM_STORE_F32;
     const double sA = p->shift_A > 0.0 ? p->shift_A : 0.5 * p->mass_A * (1.0 + p->minority);
@@ -404,6 +415,7 @@ lbm_status lbm_reset(lbm_handle* h) {
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
     if (!h) return fail(LBM_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    if (h->timed_out) return fail(LBM_ETIMEOUT, "an earlier step timed out");
     if (h->unstable) return fail(LBM_EUNSTABLE, "state is unstable");
     int64_t left = nsteps;
     while (left >= kGraphChunk) {

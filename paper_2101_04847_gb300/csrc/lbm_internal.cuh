@@ -49,7 +49,9 @@ struct Physics {
 // Geometry of one population array set.
 struct Grid {
     int nx, ny;
-    int pitch;          // elements per stored row (>= nx, multiple of 64)
+    int pitch;          // elements per stored row
+    int origin;         // element offset of column 0 in a row (128 bytes); columns
+                        // -2, -1, nx, nx+1 hold periodic copies of nx-2, nx-1, 0, 1
     size_t plane;       // elements per (component, direction) plane = ny * pitch
 };
 

@@ -20,20 +20,63 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
     sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
 }
 
+// Double-float helpers (error-free transformations, Knuth's TwoSum and the
+// FMA-based TwoProduct) used to repair the FP32 rounding of mass and momentum.
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ void df_add(DF& d, float v) {
+    const DF t = two_sum(d.hi, v);
+    d.hi = t.hi;
+    d.lo += t.lo;
+}
+// a * b with a double-float: (a.hi*b, err) as double-float
+__device__ __forceinline__ DF df_mul(DF a, float b) {
+    const float p = a.hi * b;
+    return {p, fmaf(a.hi, b, -p) + a.lo * b};
+}
+
 // Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
 // "Equilibrium distribution"): f <- f + (f^eq(rho_s, u + tau_s a_s) - f) / tau_s with
 // a_s = F_s / rho_s computed directly (no division by rho_s).
+//
+// kExact (FP32 storage): after the BGK update, the moving populations 1..4 are
+// nudged so that each component's momentum equals (1 - w) j_s + w rho_s u'_s to
+// double-float accuracy, and the rest population is set to rho_s - sum_{i>0} f*_i
+// (double-float).  Both are identities of the exact BGK update (it keeps rho_s and
+// gives that momentum); in FP32 they remove the per-site rounding of mass and of
+// the large, nearly cancelling inter-component Shan-Chen momenta, which otherwise
+// random-walks the interface position (~1e-5 of rho after 1000 steps at tau = 1).
+template <bool kExact>
 __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, const Nbr& psiB,
                                              const Physics& ph, int y, int ny, int* flag) {
-    const float rA = sum9(f[0]);
-    const float rB = sum9(f[1]);
-    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) *flag = 1;
-    float jx[2], jy[2];
+    DF rr[2], jxd[2], jyd[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]);
-        jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]);
+        if (kExact) {
+            rr[s] = {f[s][0], 0.0f};
+#pragma unroll
+            for (int i = 1; i < 9; ++i) df_add(rr[s], f[s][i]);
+            jxd[s] = {f[s][1], 0.0f};
+            df_add(jxd[s], -f[s][3]); df_add(jxd[s], f[s][5]); df_add(jxd[s], -f[s][6]);
+            df_add(jxd[s], f[s][8]); df_add(jxd[s], -f[s][7]);
+            jyd[s] = {f[s][2], 0.0f};
+            df_add(jyd[s], -f[s][4]); df_add(jyd[s], f[s][5]); df_add(jyd[s], -f[s][8]);
+            df_add(jyd[s], f[s][6]); df_add(jyd[s], -f[s][7]);
+        } else {
+            rr[s] = {sum9(f[s]), 0.0f};
+            jxd[s] = {(f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]), 0.0f};
+            jyd[s] = {(f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]), 0.0f};
+        }
     }
+    const float rA = rr[0].hi + rr[0].lo;
+    const float rB = rr[1].hi + rr[1].lo;
+    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
+    const float jx[2] = {jxd[0].hi + jxd[0].lo, jxd[1].hi + jxd[1].lo};
+    const float jy[2] = {jyd[0].hi + jyd[0].lo, jyd[1].hi + jyd[1].lo};
     const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
     const float ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
     const float uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;
@@ -55,10 +98,45 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
         const float usq = 1.5f * (vx * vx + vy * vy);
         const float om = ph.om[s];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int i = kExact ? 1 : 0; i < 9; ++i) {
             const float cu = (float)cx(i) * vx + (float)cy(i) * vy;
             const float feq = rho[s] * wf(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq);
             f[s][i] = f[s][i] + om * (feq - f[s][i]);
+        }
+        if (kExact) {
+            const float om1 = 1.0f - om;
+            // x: target (1 - w) jx + w rho vx, repaired on the pair 1 / 3
+            {
+                const DF rv = df_mul(rr[s], vx);
+                const DF a = df_mul(jxd[s], om1);
+                const DF b = df_mul(rv, om);
+                DF t = two_sum(a.hi, b.hi);
+                t.lo += a.lo + b.lo;
+                DF o = {f[s][1], 0.0f};
+                df_add(o, -f[s][3]); df_add(o, f[s][5]); df_add(o, -f[s][6]);
+                df_add(o, f[s][8]); df_add(o, -f[s][7]);
+                const float half = 0.5f * ((t.hi - o.hi) + (t.lo - o.lo));
+                f[s][1] += half;
+                f[s][3] -= half;
+            }
+            // y: pair 2 / 4
+            {
+                const DF rv = df_mul(rr[s], vy);
+                const DF a = df_mul(jyd[s], om1);
+                const DF b = df_mul(rv, om);
+                DF t = two_sum(a.hi, b.hi);
+                t.lo += a.lo + b.lo;
+                DF o = {f[s][2], 0.0f};
+                df_add(o, -f[s][4]); df_add(o, f[s][5]); df_add(o, -f[s][8]);
+                df_add(o, f[s][6]); df_add(o, -f[s][7]);
+                const float half = 0.5f * ((t.hi - o.hi) + (t.lo - o.lo));
+                f[s][2] += half;
+                f[s][4] -= half;
+            }
+            DF m = {f[s][1], 0.0f};
+#pragma unroll
+            for (int i = 2; i < 9; ++i) df_add(m, f[s][i]);
+            f[s][0] = (rr[s].hi - m.hi) + (rr[s].lo - m.lo);
         }
     }
 }
@@ -153,13 +231,204 @@ step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
             pB.N = sR[s2][1][k];     pB.S = sR[s0][1][k];
             pB.NE = sR[s2][1][k + 1]; pB.NW = sR[s2][1][k - 1];
             pB.SE = sR[s0][1][k + 1]; pB.SW = sR[s0][1][k - 1];
-            collide_site(cur, pA, pB, ph, y, g.ny, flag);
-            const size_t row = (size_t)y * g.pitch + x;
+            collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
+            store_site<T>(fout, g, y, x, cur, shift);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) cur[s][i] = nxt[s][i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Staged fused pull stream-collide.  Same sweep as step_fused_kernel, but the
+// input rows are brought into shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion tracked by one mbarrier per stage) issued by one
+// thread: row r of all 18 planes, columns [x0 - 8, x0 + 136), lands in stage
+// (r - rfirst) mod kStages.  The pulls (including the two halo columns) then read
+// shared memory, so each input value crosses HBM once per tile, and two rows
+// ahead of the sweep are always in flight.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 5;      // rows y..y+2 in use + 2 rows prefetched
+constexpr int kWinPad = 8;      // window columns left of x0 (>= 2 and 16-byte aligned for 16-bit types)
+constexpr int kWin = kThreadsX + 2 * kWinPad;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after kWaitLimit polls and raises bit 2 of the guard flag.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    atomicOr(flag, 2);
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <typename T>
+size_t staged_smem_bytes() { return (size_t)kStages * 18 * kWin * sizeof(T) + kStages * sizeof(uint64_t); }
+
+// Post-streaming populations of window column k on row yo from the staged rows.
+template <typename T>
+__device__ __forceinline__ void pull_staged(const T* __restrict__ stage, int rfirst, int yo, int ny, int k,
+                                            const float shift[2], float f[2][9]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sy = yo - cy(i);
+            const bool inside = (cy(i) == 0) || (sy >= 0 && sy < ny);
+            const int slot = ((inside ? sy : yo) - rfirst) % kStages;
+            const int plane = s * 9 + (inside ? i : opp(i));
+            const int col = inside ? k - cx(i) : k;
+            float v = to_f<T>(stage[(slot * 18 + plane) * kWin + col]);
+            if (IsShifted<T>::value) v += wf(i) * shift[s];
+            f[s][i] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX, 3)
+step_staged_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    T* stage = reinterpret_cast<T*>(dsm);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kStages * 18 * kWin * sizeof(T));
+    __shared__ float sR[4][2][kThreadsX + 2];
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * kThreadsX;
+    const int w = min(kThreadsX, g.nx - x0);
+    const int y0 = blockIdx.y * tile_y;
+    const int y1 = min(y0 + tile_y, g.ny);
+    const int rfirst = max(y0 - 2, 0);
+    const int rlast = min(y1 + 1, g.ny - 1);
+    const bool active = t < w;
+    const int x = x0 + (active ? t : w - 1);
+    const int k = kWinPad + (active ? t : w - 1);
+    const bool haloL = (t == 0);
+    const bool haloR = (t == max(w - 1, 1));
+    const bool halo = haloL || haloR;
+    const int hk = haloL ? kWinPad - 1 : kWinPad + w;
+    const int hs = haloL ? 0 : w + 1;
+    const float shift[2] = {ph.shift[0], ph.shift[1]};
+    const uint32_t row_bytes = kWin * sizeof(T);
+    const T* win = fin + (size_t)g.origin + x0 - kWinPad;
+
+    if (t == 0) {
+        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int next = rfirst;  // next row to issue (meaningful in thread 0)
+    if (t == 0) {
+        for (; next <= rlast && next < rfirst + kStages; ++next) {
+            uint64_t* b = &bar[(next - rfirst) % kStages];
+            mbar_expect_tx(b, 18 * row_bytes);
+            T* dst = stage + (size_t)((next - rfirst) % kStages) * 18 * kWin;
+            for (int p = 0; p < 18; ++p)
+                bulk_copy_g2s(dst + p * kWin, win + (size_t)p * g.plane + (size_t)next * g.pitch, row_bytes, b);
+        }
+    }
+    auto wait_row = [&](int r) {
+        if (r >= rfirst && r <= rlast)
+            mbar_wait(&bar[(r - rfirst) % kStages], (uint32_t)(((r - rfirst) / kStages) & 1), flag);
+    };
+
+    float cur[2][9];
+    {   // density of row y0 - 1 (zero on the virtual wall row)
+        const int slot = (y0 - 1) & 3;
+        float rA = 0.0f, rB = 0.0f, hA = 0.0f, hB = 0.0f;
+        if (y0 > 0) {
+            wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
+            float tmp[2][9];
+            pull_staged<T>(stage, rfirst, y0 - 1, g.ny, k, shift, tmp);
+            rA = sum9(tmp[0]); rB = sum9(tmp[1]);
+            if (halo) {
+                pull_staged<T>(stage, rfirst, y0 - 1, g.ny, hk, shift, tmp);
+                hA = sum9(tmp[0]); hB = sum9(tmp[1]);
+            }
+        }
+        if (active) { sR[slot][0][t + 1] = rA; sR[slot][1][t + 1] = rB; }
+        if (halo) { sR[slot][0][hs] = hA; sR[slot][1][hs] = hB; }
+    }
+    {   // row y0
+        const int slot = y0 & 3;
+        wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
+        pull_staged<T>(stage, rfirst, y0, g.ny, k, shift, cur);
+        if (active) { sR[slot][0][t + 1] = sum9(cur[0]); sR[slot][1][t + 1] = sum9(cur[1]); }
+        if (halo) {
+            float tmp[2][9];
+            pull_staged<T>(stage, rfirst, y0, g.ny, hk, shift, tmp);
+            sR[slot][0][hs] = sum9(tmp[0]); sR[slot][1][hs] = sum9(tmp[1]);
+        }
+    }
+    for (int y = y0; y < y1; ++y) {
+        float nxt[2][9];
+        const int sn = (y + 1) & 3;
+        if (y + 1 < g.ny) {
+            wait_row(y + 2);
+            pull_staged<T>(stage, rfirst, y + 1, g.ny, k, shift, nxt);
+            if (active) { sR[sn][0][t + 1] = sum9(nxt[0]); sR[sn][1][t + 1] = sum9(nxt[1]); }
+            if (halo) {
+                float tmp[2][9];
+                pull_staged<T>(stage, rfirst, y + 1, g.ny, hk, shift, tmp);
+                sR[sn][0][hs] = sum9(tmp[0]); sR[sn][1][hs] = sum9(tmp[1]);
+            }
+        } else {
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + row, i, cur[s][i], shift[s]);
+                for (int i = 0; i < 9; ++i) nxt[s][i] = 0.0f;
+            if (active) { sR[sn][0][t + 1] = 0.0f; sR[sn][1][t + 1] = 0.0f; }
+            if (halo) { sR[sn][0][hs] = 0.0f; sR[sn][1][hs] = 0.0f; }
+        }
+        __syncthreads();
+        // every thread is past its reads of rows < y: refill those stages
+        if (t == 0) {
+            fence_proxy_async_smem();
+            for (; next <= rlast && next - kStages <= y - 1; ++next) {
+                uint64_t* b = &bar[(next - rfirst) % kStages];
+                mbar_expect_tx(b, 18 * row_bytes);
+                T* dst = stage + (size_t)((next - rfirst) % kStages) * 18 * kWin;
+                for (int p = 0; p < 18; ++p)
+                    bulk_copy_g2s(dst + p * kWin, win + (size_t)p * g.plane + (size_t)next * g.pitch, row_bytes, b);
+            }
+        }
+        if (active) {
+            const int kk = t + 1;
+            const int s0 = (y - 1) & 3, s1 = y & 3, s2 = sn;
+            Nbr pA, pB;
+            pA.E = sR[s1][0][kk + 1]; pA.W = sR[s1][0][kk - 1];
+            pA.N = sR[s2][0][kk];     pA.S = sR[s0][0][kk];
+            pA.NE = sR[s2][0][kk + 1]; pA.NW = sR[s2][0][kk - 1];
+            pA.SE = sR[s0][0][kk + 1]; pA.SW = sR[s0][0][kk - 1];
+            pB.E = sR[s1][1][kk + 1]; pB.W = sR[s1][1][kk - 1];
+            pB.N = sR[s2][1][kk];     pB.S = sR[s0][1][kk];
+            pB.NE = sR[s2][1][kk + 1]; pB.NW = sR[s2][1][kk - 1];
+            pB.SE = sR[s0][1][kk + 1]; pB.SW = sR[s0][1][kk - 1];
+            collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
+            store_site<T>(fout, g, y, x, cur, shift);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -216,13 +485,8 @@ collide_kernel(const T* __restrict__ fin, const float* __restrict__ psi, T* __re
             p[s].S = p[s].SE = p[s].SW = 0.0f;
         }
     }
-    collide_site(f, p[0], p[1], ph, y, g.ny, flag);
-    const size_t row = (size_t)y * g.pitch + x;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + row, i, f[s][i], ph.shift[s]);
+    collide_site<IsShifted<T>::value == false>(f, p[0], p[1], ph, y, g.ny, flag);
+    store_site<T>(fout, g, y, x, f, ph.shift);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,16 +510,16 @@ __global__ void init_kernel(T* __restrict__ fout, Grid g, float sA, float sB, co
     const float shift[2] = {sA, sB};
     double here[2];
     init_rho(y0, x, y, mA, mB, eps, width, here[0], here[1]);
+    float f[2][9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int ty = y + cy(i);
         const int tx = (x + cx(i) + g.nx) % g.nx;
         double r[2] = {here[0], here[1]};
         if (ty >= 0 && ty < g.ny) init_rho(y0, tx, ty, mA, mB, eps, width, r[0], r[1]);
-        for (int s = 0; s < 2; ++s)
-            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + (size_t)y * g.pitch + x, i,
-                         (float)(wd(i) * r[s]), shift[s]);
+        for (int s = 0; s < 2; ++s) f[s][i] = (float)(wd(i) * r[s]);
     }
+    store_site<T>(fout, g, y, x, f, shift);
 }
 
 template <typename T>
@@ -280,6 +544,7 @@ __global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, fl
     if (x >= g.nx) return;
     const float shift[2] = {sA, sB};
     const size_t n = (size_t)g.nx * g.ny;
+    float f[2][9];
     for (int s = 0; s < 2; ++s) {
         for (int i = 0; i < 9; ++i) {
             const int ty = y + cy(i);
@@ -287,9 +552,10 @@ __global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, fl
             const double v = (ty >= 0 && ty < g.ny)
                 ? S[(size_t)(s * 9 + i) * n + (size_t)ty * g.nx + tx]
                 : S[(size_t)(s * 9 + opp(i)) * n + (size_t)y * g.nx + x];
-            store_pop<T>(fout + (size_t)(s * 9 + i) * g.plane + (size_t)y * g.pitch + x, i, (float)v, shift[s]);
+            f[s][i] = (float)v;
         }
     }
+    store_site<T>(fout, g, y, x, f, shift);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,6 +569,18 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         dim3 grid(bx, g.ny);
         density_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, g, L.phys);
         collide_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, (T*)L.fout, g, L.phys, L.flag);
+    } else if (kernel == LBM_KERNEL_STAGED) {
+        const int ty = L.tile_y > 0 ? L.tile_y : 32;
+        const size_t smem = staged_smem_bytes<T>();
+        static bool attr_set = false;   // one per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        dim3 grid(bx, (g.ny + ty - 1) / ty);
+        step_staged_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
     } else {
         const int ty = L.tile_y > 0 ? L.tile_y : 16;
         dim3 grid(bx, (g.ny + ty - 1) / ty);

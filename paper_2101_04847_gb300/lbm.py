@@ -15,7 +15,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"fused": 0, "two_pass": 1}
+KERNEL = {"fused": 0, "two_pass": 1, "staged": 2}
 
 
 class LbmParams(C.Structure):
