@@ -188,6 +188,30 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 /* Release the handle (and its own workspace / stream if it allocated them). */
 void lbm_destroy(lbm_handle* h);
 
+/* One time step that allocates nothing, for callers that cannot allocate device
+ * memory: code running inside a host application or framework that owns the GPU
+ * memory budget and forbids allocations outside it, or a loop that cannot take
+ * the device-wide synchronisation a cudaMalloc / cudaFree can cause.  The paper
+ * has no counterpart; this is an embedding interface.
+ *
+ * Same physics and FP32 arithmetic as lbm_step (the two-pass form: a density pass,
+ * then collision and streaming).  pops_in and pops_out are distinct device arrays
+ * of 2*9*ny*nx floats, [component][direction][y][x], holding post-streaming
+ * populations (the layout of lbm_get_populations, in FP32); pops_out receives the
+ * populations one step later.  Only nx, ny, tau_A, tau_B, G, G_wall_A, G_wall_B,
+ * g, gravity_mode and gx of *p are used; storage must be LBM_STORE_F32.
+ * cuda_stream: a cudaStream_t, or NULL for the default stream.  Asynchronous.
+ *
+ * Scratch: the densities go to a fixed device array inside the library of
+ * 2 * 2^20 floats (8 MiB), held by every GPU that loads the library until the
+ * process exits; grids with nx * ny > 2^20 are rejected with LBM_EINVAL.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress),
+ * so make the first call on each device before any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU (different streams, or
+ * threads) race and give wrong results; serialise them.  No NaN / negative-density
+ * report: use lbm_step on a handle for that. */
+lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in, float* pops_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,8 @@ lbm_status validate(const lbm_params* p) {
 
 }  // namespace
 
+void lbm::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct lbm_handle {
     lbm_params p;
     int device = 0;

@@ -8,6 +8,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -65,6 +67,9 @@ struct StepLaunch {
     int storage;         // lbm_storage
     int tile_y;
 };
+
+// message returned by lbm_last_error() on this thread (lbm_api.cu)
+void set_last_error(const std::string& msg);
 
 // step kernels (step_kernels.cu)
 cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st);

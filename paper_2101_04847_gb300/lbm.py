@@ -68,6 +68,7 @@ _PROTOS = {
     "lbm_save": (C.c_int, [_h, C.c_char_p]),
     "lbm_load": (C.c_int, [_h, C.c_char_p]),
     "lbm_destroy": (None, [_h]),
+    "lbm_step_noalloc": (C.c_int, [_P(LbmParams), C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
