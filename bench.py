@@ -242,7 +242,8 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     bytes_per_launch = BYTES_PER_SITE[args.storage] * sites
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
-    kname = {"fused": "step_fused_kernel", "staged": "step_staged_kernel", "two_pass": "collide_kernel"}[args.kernel]
+    kname = {"fused": "step_fused_kernel", "staged": "step_block_kernel", "warp": "step_warp_kernel",
+             "two_pass": "collide_kernel"}[args.kernel]
     traffic = profiled_traffic(f"{kname}:{args.storage}", args.nx, args.ny)
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": ws,
@@ -265,6 +266,100 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _splitmix64(state: int):
+    state = (state + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & ((1 << 64) - 1)
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & ((1 << 64) - 1)
+    return state, z ^ (z >> 31)
+
+
+def ensemble_members(n: int = 16, seed: int = 0) -> list[dict]:
+    """Members of the batched-ensemble workload: grids drawn uniformly from
+    {512x1024, 1024x2048, 2048x4096}, G from {0.0, 1.2, 1.4}, FP32 or FP16 storage,
+    from splitmix64(seed); member i is seeded i + 1."""
+    grids = [(512, 1024), (1024, 2048), (2048, 4096)]
+    Gs = [0.0, 1.2, 1.4]
+    st = seed
+    out = []
+    for i in range(n):
+        st, a = _splitmix64(st)
+        st, b = _splitmix64(st)
+        st, c = _splitmix64(st)
+        nx, ny = grids[a % 3]
+        G = Gs[b % 3]
+        d = dict(nx=nx, ny=ny, tau_A=1.0, tau_B=1.0, G=G, mass_A=1.0, mass_B=0.9, g=1e-5, n_modes=8, amp=2.0,
+                 width=1.5, minority=0.0 if G == 0.0 else 0.08, crop_rows=10, seed=i + 1,
+                 storage="f16" if c % 2 else "f32")
+        out.append(d)
+    return out
+
+
+def run_ensemble(args):
+    import torch
+
+    from paper_2101_04847_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    members = ensemble_members(args.ensemble)
+    lb_steps = 20
+    params = [lbm.default_params(kernel="staged", **m) for m in members]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ens = lbm.Ensemble(params, stream=stream.cuda_stream)
+    tile_y, _ = ens.tune()
+    for _ in range(args.warmup):
+        ens.step(lb_steps)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        a.record(stream)
+        for _ in range(args.steps):
+            ens.step(lb_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+    ens.sync()
+    ens_ms = a.elapsed_time(b)
+    ens.close()
+    sites = sum(m["nx"] * m["ny"] for m in members)
+    agg = sites * lb_steps * args.steps / (ens_ms * 1e-3) / 1e6
+    # the same realisations advanced one after another, each with its own solver
+    seq_ms = 0.0
+    for m in members:
+        with torch.cuda.stream(stream):
+            s = lbm.Solver(lbm.default_params(kernel="staged", tile_y=tile_y, **m))
+        for _ in range(args.warmup):
+            s.step(lb_steps)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            s.step(lb_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(b)
+        s.close()
+    seq = sites * lb_steps * args.steps / (seq_ms * 1e-3) / 1e6
+    bytes_per_update = sum(m["nx"] * m["ny"] * BYTES_PER_SITE[m["storage"]] for m in members)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bytes_per_update * lb_steps * args.steps / (ens_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(agg, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ens_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16", "data": "synthetic",
+        "config": {"workload": f"ensemble of {len(members)} realisations, grids from 512x1024/1024x2048/2048x4096, "
+                               f"G from 0/1.2/1.4, FP32 or FP16 storage, one launch per LB step",
+                   "members": [f"{m['nx']}x{m['ny']} G={m['G']} {m['storage']}" for m in members],
+                   "lb_steps_per_step": lb_steps, "tile_y": tile_y},
+        "sequential": {"value": round(seq, 1), "unit": "MLUPS", "speedup": round(agg / seq, 3)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "ensemble_step_kernel",
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "gpu_launches": lb_steps * args.steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(out), flush=True)
 
 
 def cpu_baseline(args, budget_s: float) -> dict:
@@ -322,17 +417,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
-    ap.add_argument("--kernel", choices=["fused", "two_pass", "staged"], default="staged")
+    ap.add_argument("--kernel", choices=["fused", "two_pass", "staged", "warp"], default="staged")
     ap.add_argument("--tile-y", dest="tile_y", type=int, default=0)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.ensemble:
+        run_ensemble(args)
     else:
         run_ours(args)
 

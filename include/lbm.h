@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
     LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step (global-memory pulls) */
     LBM_KERNEL_TWO_PASS = 1, /* density kernel + stream-collide kernel per step */
-    LBM_KERNEL_STAGED = 2    /* fused kernel with rows staged in shared memory by bulk async copies */
+    LBM_KERNEL_STAGED = 2,   /* fused kernel, rows staged in shared memory by bulk async copies, block-wide sweep */
+    LBM_KERNEL_WARP = 3      /* as STAGED, one independent sweep per warp (the ensemble's tile kernel) */
 } lbm_kernel;
 
 /* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
@@ -187,6 +188,42 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 
 /* Release the handle (and its own workspace / stream if it allocated them). */
 void lbm_destroy(lbm_handle* h);
+
+/* Pick the rows per tile (tile_y) of the handle's step kernel by timing candidate
+ * values on the handle's own grid, then use the fastest.  The state and the step
+ * counter are left as they were.  cache_path: NULL, or a text file of
+ * "<gpu>|<kernel>|<storage>|<nx>x<ny> <tile_y> <ms>" lines; a matching line is used
+ * without timing, a new result is appended.  Outputs may be NULL. */
+lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* tile_y, double* ms_per_step);
+
+/* ---- Ensembles of independent realisations (Section 2: at least 10 runs per
+ * experiment).  One kernel launch per time step advances every member; chunks
+ * of steps are replayed as CUDA graphs.  Members may differ in grid, physics and
+ * storage; each uses the staged kernel and its own workspace. ---- */
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* n parameter sets (1..256); tile_y of members[0] (or the default) is used for
+ * all.  cuda_stream: a cudaStream_t shared by all members, or NULL for one owned
+ * by the ensemble. */
+lbm_status lbm_ens_create(int32_t n, const lbm_params* members, void* cuda_stream, lbm_ensemble** out);
+
+/* Advance every member by nsteps (asynchronous). */
+lbm_status lbm_ens_step(lbm_ensemble* e, int64_t nsteps);
+
+/* Wait; the first non-OK member status (LBM_EUNSTABLE / LBM_ETIMEOUT) if any. */
+lbm_status lbm_ens_sync(lbm_ensemble* e);
+
+/* Borrowed handle of member i, for diagnostics, fields, populations and
+ * checkpoints; valid until lbm_ens_destroy.  lbm_step on it returns LBM_ESTATE. */
+lbm_status lbm_ens_member(lbm_ensemble* e, int32_t i, lbm_handle** out);
+
+/* Diagnostics of every member into out[0..n-1]; synchronises. */
+lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out);
+
+/* Pick tile_y for the whole ensemble by timing candidates; states are kept. */
+lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y, double* ms_per_step);
+
+void lbm_ens_destroy(lbm_ensemble* e);
 
 /* One time step that allocates nothing, for callers that cannot allocate device
  * memory: code running inside a host application or framework that owns the GPU

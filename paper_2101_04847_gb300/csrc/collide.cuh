@@ -14,63 +14,54 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
     sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
 }
 
-// Double-float helpers (error-free transformations, Knuth's TwoSum and the
-// FMA-based TwoProduct) used to repair the FP32 rounding of mass and momentum.
+// Error-free transformations (Knuth's TwoSum) used to repair the FP32 rounding of
+// mass and momentum; sums are taken as balanced trees of double-float values,
+// which keeps the dependency chains short.
 struct DF { float hi, lo; };
-__device__ __forceinline__ DF two_sum(float a, float b) {
+__device__ __forceinline__ DF df_two(float a, float b) {
     const float s = a + b;
     const float bb = s - a;
     return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ void df_add(DF& d, float v) {
-    const DF t = two_sum(d.hi, v);
-    d.hi = t.hi;
-    d.lo += t.lo;
-}
-// a * b with a double-float: (a.hi*b, err) as double-float
-__device__ __forceinline__ DF df_mul(DF a, float b) {
-    const float p = a.hi * b;
-    return {p, fmaf(a.hi, b, -p) + a.lo * b};
+__device__ __forceinline__ DF df_plus(DF a, DF b) {
+    DF s = df_two(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return s;
 }
 
 // Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
 // "Equilibrium distribution"): f <- f + (f^eq(rho_s, u + tau_s a_s) - f) / tau_s with
-// a_s = F_s / rho_s computed directly (no division by rho_s).
+// a_s = F_s / rho_s computed directly (no division by rho_s).  The equilibrium is
+// evaluated per pair of opposite directions: f^eq_i + f^eq_ibar = 2 w rho (1 + 9/2 (c.u')^2
+// - 3/2 u'^2) and f^eq_i - f^eq_ibar = 6 w rho c.u'.
 //
-// kExact (FP32 storage): after the BGK update, the moving populations 1..4 are
-// nudged so that each component's momentum equals (1 - w) j_s + w rho_s u'_s to
-// double-float accuracy, and the rest population is set to rho_s - sum_{i>0} f*_i
-// (double-float).  Both are identities of the exact BGK update (it keeps rho_s and
-// gives that momentum); in FP32 they remove the per-site rounding of mass and of
-// the large, nearly cancelling inter-component Shan-Chen momenta, which otherwise
-// random-walks the interface position (~1e-5 of rho after 1000 steps at tau = 1).
+// kExact (FP32 storage): each component's momentum after the update is summed in
+// double-float and nudged, on the pairs 1/3 and 2/4, to (1 - w) j_s + w rho_s u'_s;
+// the rest population is then set to rho_s - sum_{i>0} f*_i with both sums in
+// double-float.  Both are identities of the exact BGK update (it keeps rho_s and gives
+// that momentum); in FP32 they remove the per-site rounding of mass and of the
+// large, nearly cancelling inter-component Shan-Chen momenta, which otherwise
+// random-walks the interface (~1e-5 of rho after 1000 steps at tau = 1).
 template <bool kExact>
 __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, const Nbr& psiB,
                                              const Physics& ph, int y, int ny, int* flag) {
-    DF rr[2], jxd[2], jyd[2];
+    DF rr[2];
+    float jx[2], jy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (kExact) {
-            rr[s] = {f[s][0], 0.0f};
-#pragma unroll
-            for (int i = 1; i < 9; ++i) df_add(rr[s], f[s][i]);
-            jxd[s] = {f[s][1], 0.0f};
-            df_add(jxd[s], -f[s][3]); df_add(jxd[s], f[s][5]); df_add(jxd[s], -f[s][6]);
-            df_add(jxd[s], f[s][8]); df_add(jxd[s], -f[s][7]);
-            jyd[s] = {f[s][2], 0.0f};
-            df_add(jyd[s], -f[s][4]); df_add(jyd[s], f[s][5]); df_add(jyd[s], -f[s][8]);
-            df_add(jyd[s], f[s][6]); df_add(jyd[s], -f[s][7]);
+            const DF a = df_plus(df_two(f[s][0], f[s][1]), df_two(f[s][2], f[s][3]));
+            const DF b = df_plus(df_two(f[s][4], f[s][5]), df_two(f[s][6], f[s][7]));
+            rr[s] = df_plus(df_plus(a, b), DF{f[s][8], 0.0f});
         } else {
             rr[s] = {sum9(f[s]), 0.0f};
-            jxd[s] = {(f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]), 0.0f};
-            jyd[s] = {(f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]), 0.0f};
         }
+        jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
+        jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][7]) + (f[s][6] - f[s][8]);
     }
     const float rA = rr[0].hi + rr[0].lo;
     const float rB = rr[1].hi + rr[1].lo;
     if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
-    const float jx[2] = {jxd[0].hi + jxd[0].lo, jxd[1].hi + jxd[1].lo};
-    const float jy[2] = {jyd[0].hi + jyd[0].lo, jyd[1].hi + jyd[1].lo};
     const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
     const float ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
     const float uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;
@@ -89,47 +80,48 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
     for (int s = 0; s < 2; ++s) {
         const float vx = ux + ph.tau[s] * ax[s];
         const float vy = uy + ph.tau[s] * ay[s];
-        const float usq = 1.5f * (vx * vx + vy * vy);
         const float om = ph.om[s];
+        const float one_minus_usq = 1.0f - 1.5f * (vx * vx + vy * vy);
+        const float r9 = rho[s] * (1.0f / 9.0f);
+        const float r36 = rho[s] * (1.0f / 36.0f);
+        float feq[9];
+        feq[0] = rho[s] * (4.0f / 9.0f) * one_minus_usq;
+        {   // pairs (1,3), (2,4), (5,7), (6,8)
+            const float c[4] = {vx, vy, vx + vy, vy - vx};
+            const float r[4] = {r9, r9, r36, r36};
+            const int a[4] = {1, 2, 5, 6}, b[4] = {3, 4, 7, 8};
 #pragma unroll
-        for (int i = kExact ? 1 : 0; i < 9; ++i) {
-            const float cu = (float)cx(i) * vx + (float)cy(i) * vy;
-            const float feq = rho[s] * wf(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq);
-            f[s][i] = f[s][i] + om * (feq - f[s][i]);
+            for (int q = 0; q < 4; ++q) {
+                const float sym = r[q] * fmaf(4.5f * c[q], c[q], one_minus_usq);
+                const float anti = r[q] * (3.0f * c[q]);
+                feq[a[q]] = sym + anti;
+                feq[b[q]] = sym - anti;
+            }
         }
+#pragma unroll
+        for (int i = kExact ? 1 : 0; i < 9; ++i) f[s][i] = fmaf(om, feq[i] - f[s][i], f[s][i]);
         if (kExact) {
             const float om1 = 1.0f - om;
             // x: target (1 - w) jx + w rho vx, repaired on the pair 1 / 3
             {
-                const DF rv = df_mul(rr[s], vx);
-                const DF a = df_mul(jxd[s], om1);
-                const DF b = df_mul(rv, om);
-                DF t = two_sum(a.hi, b.hi);
-                t.lo += a.lo + b.lo;
-                DF o = {f[s][1], 0.0f};
-                df_add(o, -f[s][3]); df_add(o, f[s][5]); df_add(o, -f[s][6]);
-                df_add(o, f[s][8]); df_add(o, -f[s][7]);
-                const float half = 0.5f * ((t.hi - o.hi) + (t.lo - o.lo));
+                const float t = fmaf(om1, jx[s], om * (rho[s] * vx));
+                const DF o = df_plus(df_plus(df_two(f[s][1], -f[s][3]), df_two(f[s][5], -f[s][7])),
+                                     df_two(f[s][8], -f[s][6]));
+                const float half = 0.5f * ((t - o.hi) - o.lo);
                 f[s][1] += half;
                 f[s][3] -= half;
             }
             // y: pair 2 / 4
             {
-                const DF rv = df_mul(rr[s], vy);
-                const DF a = df_mul(jyd[s], om1);
-                const DF b = df_mul(rv, om);
-                DF t = two_sum(a.hi, b.hi);
-                t.lo += a.lo + b.lo;
-                DF o = {f[s][2], 0.0f};
-                df_add(o, -f[s][4]); df_add(o, f[s][5]); df_add(o, -f[s][8]);
-                df_add(o, f[s][6]); df_add(o, -f[s][7]);
-                const float half = 0.5f * ((t.hi - o.hi) + (t.lo - o.lo));
+                const float t = fmaf(om1, jy[s], om * (rho[s] * vy));
+                const DF o = df_plus(df_plus(df_two(f[s][2], -f[s][4]), df_two(f[s][5], -f[s][7])),
+                                     df_two(f[s][6], -f[s][8]));
+                const float half = 0.5f * ((t - o.hi) - o.lo);
                 f[s][2] += half;
                 f[s][4] -= half;
             }
-            DF m = {f[s][1], 0.0f};
-#pragma unroll
-            for (int i = 2; i < 9; ++i) df_add(m, f[s][i]);
+            const DF m = df_plus(df_plus(df_two(f[s][1], f[s][2]), df_two(f[s][3], f[s][4])),
+                                 df_plus(df_two(f[s][5], f[s][6]), df_two(f[s][7], f[s][8])));
             f[s][0] = (rr[s].hi - m.hi) + (rr[s].lo - m.lo);
         }
     }

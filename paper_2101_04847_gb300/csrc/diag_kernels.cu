@@ -330,6 +330,7 @@ size_t diag_partials_doubles(int nx, int ny) {
 }
 
 cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st) {
+    (void)cudaGetLastError();   // a launch reports only its own error
     DiagArgs a = make_args(D);
     // The velocity gradient terms of D3/D4 need u two rows outside the averaged rows and
     // u needs rho one row further out; crop >= 3 keeps all of them inside the grid.
@@ -344,6 +345,7 @@ cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st) {
 }
 
 cudaError_t launch_fields(const DiagLaunch& D, double* /*unused*/, cudaStream_t st) {
+    (void)cudaGetLastError();
     DiagArgs a = make_args(D);
     cudaError_t e = moments(D, a, st);
     if (e != cudaSuccess) return e;

@@ -4,6 +4,7 @@
 // step_kernels.cu and diag_kernels.cu.
 #include "lbm_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -83,9 +84,9 @@ struct Layout {
 Layout make_layout(const lbm_params& p) {
     Layout L;
     // column 0 sits 128 bytes into each row; the row leaves room for the staged
-    // kernel's windows (columns -8 .. roundup(nx, 128) + 8) and the ghost copies
+    // kernel's windows (up to 144 columns from x0 - 10, x0 < nx) and the ghost copies
     L.origin = (int)(128 / elem_size(p.storage));
-    L.pitch = (p.nx + lbm::kThreadsX - 1) / lbm::kThreadsX * lbm::kThreadsX + 2 * L.origin;
+    L.pitch = (L.origin + p.nx + 160 + 63) / 64 * 64;
     L.plane = (size_t)p.ny * L.pitch;
     L.pop_bytes = 18 * L.plane * elem_size(p.storage);
     const size_t n = (size_t)p.nx * p.ny;
@@ -93,8 +94,11 @@ Layout make_layout(const lbm_params& p) {
     L.pops[0] = off; off = align_up(off + L.pop_bytes);
     L.pops[1] = off; off = align_up(off + L.pop_bytes);
     L.psi = off; off = align_up(off + 2 * L.plane * sizeof(float));
-    const size_t scratch_d = std::max(lbm::diag_scratch_doubles(p.nx, p.ny), (size_t)18 * n);
-    L.scratch = off; off = align_up(off + scratch_d * sizeof(double));
+    // scratch: diagnostics fields, host staging (18 doubles per site), or a saved copy
+    // of one population buffer (tuning)
+    const size_t scratch_b = std::max({lbm::diag_scratch_doubles(p.nx, p.ny) * sizeof(double),
+                                       (size_t)18 * n * sizeof(double), L.pop_bytes});
+    L.scratch = off; off = align_up(off + scratch_b);
     L.partials = off; off = align_up(off + lbm::diag_partials_doubles(p.nx, p.ny) * sizeof(double));
     L.out = off; off = align_up(off + (lbm::kDiagTerms + (size_t)p.ny) * sizeof(double));
     L.flag = off; off = align_up(off + 16);
@@ -114,7 +118,7 @@ lbm_status validate(const lbm_params* p) {
     if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
     if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny");
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
-    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_STAGED) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_WARP) return fail(LBM_EINVAL, "unknown kernel");
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
     const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
@@ -143,6 +147,7 @@ struct lbm_handle {
     int64_t step = 0;
     bool unstable = false;
     bool timed_out = false;
+    bool in_ensemble = false;     // stepped by its ensemble only
     double* host_out = nullptr;   // pinned, kDiagTerms + ny doubles
     std::vector<double> last_rows;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -259,6 +264,125 @@ lbm_status get_graph(lbm_handle* h, int parity, cudaGraphExec_t* out) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// internal accessors (ensemble.cu) and the tile tuner
+// ---------------------------------------------------------------------------
+namespace lbm {
+void* handle_buffer(lbm_handle* h, int k) { return h->pops(k); }
+int handle_parity(lbm_handle* h) { return h->cur; }
+Grid handle_grid(lbm_handle* h) { return h->grid; }
+Physics handle_phys(lbm_handle* h) { return h->phys; }
+int* handle_flag(lbm_handle* h) { return h->flag(); }
+const lbm_params& handle_params(lbm_handle* h) { return h->p; }
+void handle_set_ensemble(lbm_handle* h, bool on) { h->in_ensemble = on; }
+void handle_advance(lbm_handle* h, int64_t n) {
+    h->step += n;
+    h->cur ^= (int)(n & 1);
+}
+lbm_status handle_check(lbm_handle* h) { return check_flag(h); }
+// copy the current population buffer to the scratch region / back (state kept while tuning)
+cudaError_t handle_save_state(lbm_handle* h) {
+    return cudaMemcpyAsync(h->scratch(), h->pops(h->cur), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+}
+cudaError_t handle_restore_state(lbm_handle* h) {
+    return cudaMemcpyAsync(h->pops(h->cur), h->scratch(), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+}
+}  // namespace lbm
+
+namespace {
+
+std::string tune_key(const lbm_handle* h) {
+    cudaDeviceProp prop;
+    std::string dev = cudaGetDeviceProperties(&prop, h->device) == cudaSuccess ? prop.name : "unknown";
+    for (char& c : dev)
+        if (c == ' ') c = '_';
+    return dev + "|" + std::to_string(h->p.kernel) + "|" + std::to_string(h->p.storage) + "|" +
+           std::to_string(h->p.nx) + "x" + std::to_string(h->p.ny);
+}
+
+bool cache_lookup(const char* path, const std::string& key, int* tile_y, double* ms) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char k[512];
+    int ty = 0;
+    double t = 0.0;
+    bool found = false;
+    while (std::fscanf(f, "%511s %d %lf", k, &ty, &t) == 3)
+        if (key == k) {
+            *tile_y = ty;
+            *ms = t;
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, int tile_y, double ms) {
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %.6f\n", key.c_str(), tile_y, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* tile_y_out, double* ms_out) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (h->in_ensemble) return fail(LBM_ESTATE, "tune the ensemble with lbm_ens_tune");
+    const std::string key = tune_key(h);
+    int best_ty = 0;
+    double best_ms = 0.0;
+    if (cache_lookup(cache_path, key, &best_ty, &best_ms)) {
+        h->p.tile_y = best_ty;
+        destroy_graphs(h);
+    } else {
+        const int cand[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128};
+        cudaEvent_t a, b;
+        LBM_TRY(cudaEventCreate(&a), "event");
+        LBM_TRY(cudaEventCreate(&b), "event");
+        LBM_TRY(lbm::handle_save_state(h), "save state");
+        const int cur0 = h->cur;
+        best_ms = 1e30;
+        for (int ty : cand) {
+            if (ty > h->p.ny && ty != cand[0]) break;
+            h->p.tile_y = ty;
+            const int reps = 10;
+            lbm_status st = launch_steps(h, 2);
+            if (st == LBM_OK) {
+                cudaEventRecord(a, h->stream);
+                st = launch_steps(h, reps);
+                cudaEventRecord(b, h->stream);
+            }
+            if (st != LBM_OK) {
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                return st;
+            }
+            LBM_TRY(cudaEventSynchronize(b), "sync");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            // back to the saved state
+            h->cur = cur0;
+            LBM_TRY(lbm::handle_restore_state(h), "restore state");
+            if (ms / reps < best_ms) {
+                best_ms = ms / reps;
+                best_ty = ty;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+        h->p.tile_y = best_ty;
+        destroy_graphs(h);
+        cache_store(cache_path, key, best_ty, best_ms);
+    }
+    if (tile_y_out) *tile_y_out = best_ty;
+    if (ms_out) *ms_out = best_ms;
+    return LBM_OK;
+}
 
 extern "C" {
 
@@ -417,6 +541,7 @@ lbm_status lbm_reset(lbm_handle* h) {
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
     if (!h) return fail(LBM_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    if (h->in_ensemble) return fail(LBM_ESTATE, "this handle is an ensemble member: step it with lbm_ens_step");
     if (h->timed_out) return fail(LBM_ETIMEOUT, "an earlier step timed out");
     if (h->unstable) return fail(LBM_EUNSTABLE, "state is unstable");
     int64_t left = nsteps;

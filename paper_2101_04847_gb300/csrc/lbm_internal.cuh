@@ -68,6 +68,36 @@ struct StepLaunch {
     int tile_y;
 };
 
+// One member of an ensemble launch (device-side table entry).
+struct EnsMember {
+    Grid grid;
+    Physics phys;
+    void* buf[2];        // the two population buffers (input = buf[parity])
+    int* flag;           // the member's guard flag
+    int storage;         // lbm_storage
+    int tile_y;          // rows per warp tile
+    int tiles_x;         // warp tiles along x
+    int tile_begin;      // index of the member's first tile in the flat list
+};
+
+// ensemble / tiling helpers (step_kernels.cu)
+int warp_tiles(const Grid& g, int tile_y, int* tiles_x);
+int default_tile_y();
+cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, cudaStream_t st);
+
+// handle accessors for the ensemble (lbm_api.cu)
+void* handle_buffer(lbm_handle* h, int k);
+int handle_parity(lbm_handle* h);
+Grid handle_grid(lbm_handle* h);
+Physics handle_phys(lbm_handle* h);
+int* handle_flag(lbm_handle* h);
+const lbm_params& handle_params(lbm_handle* h);
+void handle_set_ensemble(lbm_handle* h, bool on);
+void handle_advance(lbm_handle* h, int64_t n);
+lbm_status handle_check(lbm_handle* h);
+cudaError_t handle_save_state(lbm_handle* h);
+cudaError_t handle_restore_state(lbm_handle* h);
+
 // message returned by lbm_last_error() on this thread (lbm_api.cu)
 void set_last_error(const std::string& msg);
 

@@ -113,18 +113,26 @@ step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
 }
 
 // ---------------------------------------------------------------------------
-// Staged fused pull stream-collide.  Same sweep as step_fused_kernel, but the
-// input rows are brought into shared memory by bulk asynchronous copies
-// (cp.async.bulk, completion tracked by one mbarrier per stage) issued by one
-// thread: row r of all 18 planes, columns [x0 - 8, x0 + 136), lands in stage
-// (r - rfirst) mod kStages.  The pulls (including the two halo columns) then read
-// shared memory, so each input value crosses HBM once per tile, and two rows
-// ahead of the sweep are always in flight.
+// Staged fused pull stream-collide, one independent sweep per warp.
+//
+// A warp owns 30 columns [xw, xw + 30) and tile_y rows; lane l handles column
+// xw - 1 + l, so lanes 0 and 31 only supply the halo densities of their
+// neighbours.  The warp brings its input rows into its own shared-memory ring
+// with bulk asynchronous copies (cp.async.bulk, one mbarrier per stage, issued by
+// lane 0): row r of all 18 planes, a 16-byte aligned window of kWinW(T) columns
+// covering [xw - 2, xw + 32), lands in stage (q0 + r - rfirst) mod kStages.  The
+// densities of rows y-1, y, y+1 stay in registers and the x-neighbours come by
+// warp shuffles, so no block-wide barrier is ever needed; a warp refills a stage
+// after __syncwarp() once all its lanes have read it.  Three input rows are in
+// flight ahead of the three in use.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 5;      // rows y..y+2 in use + 2 rows prefetched
-constexpr int kWinPad = 8;      // window columns left of x0 (>= 2 and 16-byte aligned for 16-bit types)
-constexpr int kWin = kThreadsX + 2 * kWinPad;
+constexpr int kStages = 6;     // rows y..y+2 in use + 3 rows prefetched
+constexpr int kWarpOwned = 30;
+constexpr int kWarpsPerBlock = kThreadsX / 32;
 constexpr uint32_t kWaitLimit = 1u << 22;
+template <typename T> struct WinW { static constexpr int value = 40; };   // 160 B rows (FP32)
+template <> struct WinW<__half> { static constexpr int value = 48; };     // 96 B rows
+template <> struct WinW<__nv_bfloat16> { static constexpr int value = 48; };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -157,154 +165,363 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Dynamic shared memory of one warp: kStages mbarriers, then the row ring.
 template <typename T>
-size_t staged_smem_bytes() { return (size_t)kStages * 18 * kWin * sizeof(T) + kStages * sizeof(uint64_t); }
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+    return 128 + (size_t)kStages * 18 * WinW<T>::value * sizeof(T);
+}
+template <typename T>
+size_t warp_kernel_smem_bytes() { return kWarpsPerBlock * warp_smem_bytes<T>(); }
 
-// Post-streaming populations of window column k on row yo from the staged rows.
+// Post-streaming populations of window column k on row yo from the stages holding
+// rows yo-1 (S), yo (C) and yo+1 (N); on the wall rows the populations coming from
+// outside are the bounced-back ones of row yo.
 template <typename T>
-__device__ __forceinline__ void pull_staged(const T* __restrict__ stage, int rfirst, int yo, int ny, int k,
+__device__ __forceinline__ void pull_staged(const T* __restrict__ stS, const T* __restrict__ stC,
+                                            const T* __restrict__ stN, bool bottom, bool top, int k,
                                             const float shift[2], float f[2][9]) {
+    constexpr int W = WinW<T>::value;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const int sy = yo - cy(i);
-            const bool inside = (cy(i) == 0) || (sy >= 0 && sy < ny);
-            const int slot = ((inside ? sy : yo) - rfirst) % kStages;
-            const int plane = s * 9 + (inside ? i : opp(i));
-            const int col = inside ? k - cx(i) : k;
-            float v = to_f<T>(stage[(slot * 18 + plane) * kWin + col]);
-            if (IsShifted<T>::value) v += wf(i) * shift[s];
-            f[s][i] = v;
+            const int pl = s * 9 + i;
+            T v;
+            if (cy(i) == 0) {
+                v = stC[pl * W + k - cx(i)];
+            } else if (cy(i) == 1) {
+                v = bottom ? stC[(s * 9 + opp(i)) * W + k] : stS[pl * W + k - cx(i)];
+            } else {
+                v = top ? stC[(s * 9 + opp(i)) * W + k] : stN[pl * W + k - cx(i)];
+            }
+            float fv = to_f<T>(v);
+            if (IsShifted<T>::value) fv += wf(i) * shift[s];
+            f[s][i] = fv;
+        }
+    }
+}
+
+// One warp tile (tx, ty): `my` is the warp's shared-memory region.
+template <typename T>
+__device__ __forceinline__ void warp_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
+                                          const Physics& ph, int tile_y, int tx, int ty, unsigned char* my,
+                                          int* flag) {
+    constexpr int W = WinW<T>::value;
+    const int lane = threadIdx.x & 31;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(my);
+    T* stage = reinterpret_cast<T*>(my + 128);
+    const int xw = tx * kWarpOwned;
+    const int y0 = ty * tile_y;
+    const int y1 = min(y0 + tile_y, g.ny);
+    const int rfirst = max(y0 - 2, 0);
+    const int rlast = min(y1 + 1, g.ny - 1);
+    const int x = xw - 1 + lane;
+    const bool owner = lane >= 1 && lane <= kWarpOwned && x < g.nx;
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    const int e0 = g.origin + xw - 2;
+    const int slack = e0 % kAlign;
+    const int k = lane + 1 + slack;                 // window column of this lane's site
+    const T* win = fin + (e0 - slack);
+    const float shift[2] = {ph.shift[0], ph.shift[1]};
+    const uint32_t row_bytes = W * sizeof(T);
+
+    if (lane == 0) {
+        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    int next = rfirst;  // next row to issue (lane 0)
+    auto issue = [&](int r) {
+        const int j = (r - rfirst) % kStages;
+        uint64_t* b = &bar[j];
+        mbar_expect_tx(b, 18 * row_bytes);
+        T* dst = stage + (size_t)j * 18 * W;
+        const T* src = win + (size_t)r * g.pitch;
+#pragma unroll 1
+        for (int p = 0; p < 18; ++p) bulk_copy_g2s(dst + p * W, src + (size_t)p * g.plane, row_bytes, b);
+    };
+    if (lane == 0)
+        for (; next <= rlast && next < rfirst + kStages; ++next) issue(next);
+    auto wait_row = [&](int r) {
+        if (r >= rfirst && r <= rlast)
+            mbar_wait(&bar[(r - rfirst) % kStages], (uint32_t)(((r - rfirst) / kStages) & 1), flag);
+    };
+    auto stage_of = [&](int r) -> const T* {
+        const int rr = min(max(r, rfirst), rlast);
+        return stage + (size_t)((rr - rfirst) % kStages) * 18 * W;
+    };
+    auto pull_row = [&](int yo, float f[2][9]) {
+        pull_staged<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
+    };
+    // After the reads of row yo (which used input rows up to yo + 1), input rows
+    // <= yo - 1 are no longer needed: refill their stages.
+    auto refill = [&](int yo) {
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            for (; next <= rlast && next - kStages <= yo - 1; ++next) issue(next);
+        }
+    };
+
+    float fa[2][9], fb[2][9];
+    float rm[2] = {0.0f, 0.0f};   // densities of row y - 1 (zero on the virtual wall row)
+    if (y0 > 0) {
+        wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
+        pull_row(y0 - 1, fb);
+        rm[0] = sum9(fb[0]); rm[1] = sum9(fb[1]);
+    }
+    wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
+    pull_row(y0, fa);
+    float rc[2] = {sum9(fa[0]), sum9(fa[1])};      // row y
+    refill(y0);
+
+    auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
+        float rp[2] = {0.0f, 0.0f};                 // row y + 1
+        if (y + 1 < g.ny) {
+            wait_row(y + 2);
+            pull_row(y + 1, nxt);
+            rp[0] = sum9(nxt[0]); rp[1] = sum9(nxt[1]);
+        }
+        refill(y + 1);
+        Nbr p[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            p[s].S = rm[s]; p[s].N = rp[s];
+            p[s].W = __shfl_up_sync(0xffffffffu, rc[s], 1);
+            p[s].E = __shfl_down_sync(0xffffffffu, rc[s], 1);
+            p[s].SW = __shfl_up_sync(0xffffffffu, rm[s], 1);
+            p[s].SE = __shfl_down_sync(0xffffffffu, rm[s], 1);
+            p[s].NW = __shfl_up_sync(0xffffffffu, rp[s], 1);
+            p[s].NE = __shfl_down_sync(0xffffffffu, rp[s], 1);
+        }
+        if (owner) {
+            collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
+            store_site<T>(fout, g, y, x, cur, shift);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
+    };
+    for (int y = y0; y < y1; y += 2) {
+        row(y, fa, fb);
+        if (y + 1 < y1) row(y + 1, fb, fa);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX, 4)
+step_warp_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y,
+                   int tiles_x, int tiles, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * kWarpsPerBlock + warp;
+    if (tile >= tiles) return;                      // whole warp leaves together
+    warp_tile<T>(fin, fout, g, ph, tile_y, tile % tiles_x, tile / tiles_x,
+                 dsm + (size_t)warp * warp_smem_bytes<T>(), flag);
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble step: one launch advances every member by one time step.  Warp w of
+// the launch takes tile w of the flat list that concatenates the members' warp
+// tiles (members may differ in grid, physics and storage type); no member waits
+// for another, so uneven grids need no barrier.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreadsX, 4)
+ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int total_tiles, int parity) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * kWarpsPerBlock + warp;
+    if (tile >= total_tiles) return;
+    int m = 0;
+    while (m + 1 < n && members[m + 1].tile_begin <= tile) ++m;
+    const EnsMember& M = members[m];
+    const int local = tile - M.tile_begin;
+    const int tx = local % M.tiles_x, ty = local / M.tiles_x;
+    unsigned char* my = dsm + (size_t)warp * warp_smem_bytes<float>();
+    const void* fin = M.buf[parity];
+    void* fout = M.buf[parity ^ 1];
+    switch (M.storage) {
+        case LBM_STORE_F16:
+            warp_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, M.tile_y, tx, ty, my, M.flag);
+            break;
+        case LBM_STORE_BF16:
+            warp_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, M.phys, M.tile_y, tx, ty,
+                                     my, M.flag);
+            break;
+        default:
+            warp_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, M.tile_y, tx, ty, my, M.flag);
+    }
+}
+
+int warp_tiles(const Grid& g, int tile_y, int* tiles_x) {
+    const int tx = (g.nx + kWarpOwned - 1) / kWarpOwned;
+    if (tiles_x) *tiles_x = tx;
+    return tx * ((g.ny + tile_y - 1) / tile_y);
+}
+
+int default_tile_y() { return 32; }
+
+cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, cudaStream_t st) {
+    (void)cudaGetLastError();
+    const size_t smem = kWarpsPerBlock * warp_smem_bytes<float>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int blocks = (total_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    ensemble_step_kernel<<<blocks, kThreadsX, smem, st>>>(d_members, n, total_tiles, parity);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Block-staged fused pull stream-collide.  A block of 128 threads owns 126
+// columns [x0, x0 + 126) and tile_y rows; thread t handles column x0 - 1 + t, so
+// the two edge threads only supply the halo densities of their neighbours.  Input
+// rows are brought into shared memory by bulk asynchronous copies (cp.async.bulk,
+// one mbarrier per stage) issued by one thread: row r of all 18 planes, a 16-byte
+// aligned window of kBlockWin columns covering [x0 - 3, x0 + 129), lands in stage
+// (r - rfirst) mod kBlockStages.  All pulls read shared memory; each input value
+// crosses HBM once per tile and two rows ahead of the sweep are in flight.  The
+// densities of three rows are exchanged through a shared-memory ring (one block
+// barrier per row).
+// ---------------------------------------------------------------------------
+constexpr int kBlockStages = 5;
+constexpr int kOwned = kThreadsX - 2;
+constexpr int kBlockWin = 144;   // >= 128 + 2 + 7 (alignment slack), 16-byte multiple for 2- and 4-byte types
+
+template <typename T>
+size_t block_smem_bytes() { return (size_t)kBlockStages * 18 * kBlockWin * sizeof(T) + kBlockStages * sizeof(uint64_t); }
+
+// Post-streaming populations of window column k on row yo from the stages holding
+// rows yo-1 (S), yo (C), yo+1 (N) (bounce-back on the wall rows).
+template <typename T>
+__device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* __restrict__ stC,
+                                           const T* __restrict__ stN, bool bottom, bool top, int k,
+                                           const float shift[2], float f[2][9]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int pl = s * 9 + i;
+            T v;
+            if (cy(i) == 0) {
+                v = stC[pl * kBlockWin + k - cx(i)];
+            } else if (cy(i) == 1) {
+                v = bottom ? stC[(s * 9 + opp(i)) * kBlockWin + k] : stS[pl * kBlockWin + k - cx(i)];
+            } else {
+                v = top ? stC[(s * 9 + opp(i)) * kBlockWin + k] : stN[pl * kBlockWin + k - cx(i)];
+            }
+            float fv = to_f<T>(v);
+            if (IsShifted<T>::value) fv += wf(i) * shift[s];
+            f[s][i] = fv;
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsX, 3)
-step_staged_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+__global__ void __launch_bounds__(kThreadsX, 4)
+step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
     extern __shared__ __align__(128) unsigned char dsm[];
     T* stage = reinterpret_cast<T*>(dsm);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kStages * 18 * kWin * sizeof(T));
-    __shared__ float sR[4][2][kThreadsX + 2];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kBlockStages * 18 * kBlockWin * sizeof(T));
+    __shared__ float sR[4][2][kThreadsX];
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * kThreadsX;
-    const int w = min(kThreadsX, g.nx - x0);
+    const int x0 = blockIdx.x * kOwned;
     const int y0 = blockIdx.y * tile_y;
     const int y1 = min(y0 + tile_y, g.ny);
     const int rfirst = max(y0 - 2, 0);
     const int rlast = min(y1 + 1, g.ny - 1);
-    const bool active = t < w;
-    const int x = x0 + (active ? t : w - 1);
-    const int k = kWinPad + (active ? t : w - 1);
-    const bool haloL = (t == 0);
-    const bool haloR = (t == max(w - 1, 1));
-    const bool halo = haloL || haloR;
-    const int hk = haloL ? kWinPad - 1 : kWinPad + w;
-    const int hs = haloL ? 0 : w + 1;
+    const int x = x0 - 1 + t;
+    const bool owner = t >= 1 && t <= kOwned && x < g.nx;
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    const int e0 = g.origin + x0 - 3;
+    const int slack = e0 % kAlign;
+    const int k = t + 2 + slack;
+    const T* win = fin + (e0 - slack);
     const float shift[2] = {ph.shift[0], ph.shift[1]};
-    const uint32_t row_bytes = kWin * sizeof(T);
-    const T* win = fin + (size_t)g.origin + x0 - kWinPad;
+    const uint32_t row_bytes = kBlockWin * sizeof(T);
 
     if (t == 0) {
-        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
+        for (int j = 0; j < kBlockStages; ++j) mbar_init(&bar[j], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    int next = rfirst;  // next row to issue (meaningful in thread 0)
-    if (t == 0) {
-        for (; next <= rlast && next < rfirst + kStages; ++next) {
-            uint64_t* b = &bar[(next - rfirst) % kStages];
-            mbar_expect_tx(b, 18 * row_bytes);
-            T* dst = stage + (size_t)((next - rfirst) % kStages) * 18 * kWin;
-            for (int p = 0; p < 18; ++p)
-                bulk_copy_g2s(dst + p * kWin, win + (size_t)p * g.plane + (size_t)next * g.pitch, row_bytes, b);
-        }
-    }
+    int next = rfirst;  // next row to issue (thread 0)
+    auto issue = [&](int r) {
+        const int j = (r - rfirst) % kBlockStages;
+        uint64_t* b = &bar[j];
+        mbar_expect_tx(b, 18 * row_bytes);
+        T* dst = stage + (size_t)j * 18 * kBlockWin;
+        const T* src = win + (size_t)r * g.pitch;
+#pragma unroll 1
+        for (int p = 0; p < 18; ++p) bulk_copy_g2s(dst + p * kBlockWin, src + (size_t)p * g.plane, row_bytes, b);
+    };
+    if (t == 0)
+        for (; next <= rlast && next < rfirst + kBlockStages; ++next) issue(next);
     auto wait_row = [&](int r) {
         if (r >= rfirst && r <= rlast)
-            mbar_wait(&bar[(r - rfirst) % kStages], (uint32_t)(((r - rfirst) / kStages) & 1), flag);
+            mbar_wait(&bar[(r - rfirst) % kBlockStages], (uint32_t)(((r - rfirst) / kBlockStages) & 1), flag);
+    };
+    auto stage_of = [&](int r) -> const T* {
+        const int rr = min(max(r, rfirst), rlast);
+        return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * kBlockWin;
+    };
+    auto pull_row = [&](int yo, float f[2][9]) {
+        pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
     };
 
-    float cur[2][9];
+    float fa[2][9], fb[2][9];
     {   // density of row y0 - 1 (zero on the virtual wall row)
         const int slot = (y0 - 1) & 3;
-        float rA = 0.0f, rB = 0.0f, hA = 0.0f, hB = 0.0f;
+        float rA = 0.0f, rB = 0.0f;
         if (y0 > 0) {
             wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
-            float tmp[2][9];
-            pull_staged<T>(stage, rfirst, y0 - 1, g.ny, k, shift, tmp);
-            rA = sum9(tmp[0]); rB = sum9(tmp[1]);
-            if (halo) {
-                pull_staged<T>(stage, rfirst, y0 - 1, g.ny, hk, shift, tmp);
-                hA = sum9(tmp[0]); hB = sum9(tmp[1]);
-            }
+            pull_row(y0 - 1, fb);
+            rA = sum9(fb[0]); rB = sum9(fb[1]);
         }
-        if (active) { sR[slot][0][t + 1] = rA; sR[slot][1][t + 1] = rB; }
-        if (halo) { sR[slot][0][hs] = hA; sR[slot][1][hs] = hB; }
+        sR[slot][0][t] = rA; sR[slot][1][t] = rB;
     }
-    {   // row y0
-        const int slot = y0 & 3;
-        wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
-        pull_staged<T>(stage, rfirst, y0, g.ny, k, shift, cur);
-        if (active) { sR[slot][0][t + 1] = sum9(cur[0]); sR[slot][1][t + 1] = sum9(cur[1]); }
-        if (halo) {
-            float tmp[2][9];
-            pull_staged<T>(stage, rfirst, y0, g.ny, hk, shift, tmp);
-            sR[slot][0][hs] = sum9(tmp[0]); sR[slot][1][hs] = sum9(tmp[1]);
-        }
-    }
-    for (int y = y0; y < y1; ++y) {
-        float nxt[2][9];
+    wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
+    pull_row(y0, fa);
+    sR[y0 & 3][0][t] = sum9(fa[0]);
+    sR[y0 & 3][1][t] = sum9(fa[1]);
+
+    auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
         const int sn = (y + 1) & 3;
         if (y + 1 < g.ny) {
             wait_row(y + 2);
-            pull_staged<T>(stage, rfirst, y + 1, g.ny, k, shift, nxt);
-            if (active) { sR[sn][0][t + 1] = sum9(nxt[0]); sR[sn][1][t + 1] = sum9(nxt[1]); }
-            if (halo) {
-                float tmp[2][9];
-                pull_staged<T>(stage, rfirst, y + 1, g.ny, hk, shift, tmp);
-                sR[sn][0][hs] = sum9(tmp[0]); sR[sn][1][hs] = sum9(tmp[1]);
-            }
+            pull_row(y + 1, nxt);
+            sR[sn][0][t] = sum9(nxt[0]);
+            sR[sn][1][t] = sum9(nxt[1]);
         } else {
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) nxt[s][i] = 0.0f;
-            if (active) { sR[sn][0][t + 1] = 0.0f; sR[sn][1][t + 1] = 0.0f; }
-            if (halo) { sR[sn][0][hs] = 0.0f; sR[sn][1][hs] = 0.0f; }
+            sR[sn][0][t] = 0.0f;
+            sR[sn][1][t] = 0.0f;
         }
         __syncthreads();
         // every thread is past its reads of rows < y: refill those stages
         if (t == 0) {
             fence_proxy_async_smem();
-            for (; next <= rlast && next - kStages <= y - 1; ++next) {
-                uint64_t* b = &bar[(next - rfirst) % kStages];
-                mbar_expect_tx(b, 18 * row_bytes);
-                T* dst = stage + (size_t)((next - rfirst) % kStages) * 18 * kWin;
-                for (int p = 0; p < 18; ++p)
-                    bulk_copy_g2s(dst + p * kWin, win + (size_t)p * g.plane + (size_t)next * g.pitch, row_bytes, b);
-            }
+            for (; next <= rlast && next - kBlockStages <= y - 1; ++next) issue(next);
         }
-        if (active) {
-            const int kk = t + 1;
+        if (owner) {
             const int s0 = (y - 1) & 3, s1 = y & 3, s2 = sn;
             Nbr pA, pB;
-            pA.E = sR[s1][0][kk + 1]; pA.W = sR[s1][0][kk - 1];
-            pA.N = sR[s2][0][kk];     pA.S = sR[s0][0][kk];
-            pA.NE = sR[s2][0][kk + 1]; pA.NW = sR[s2][0][kk - 1];
-            pA.SE = sR[s0][0][kk + 1]; pA.SW = sR[s0][0][kk - 1];
-            pB.E = sR[s1][1][kk + 1]; pB.W = sR[s1][1][kk - 1];
-            pB.N = sR[s2][1][kk];     pB.S = sR[s0][1][kk];
-            pB.NE = sR[s2][1][kk + 1]; pB.NW = sR[s2][1][kk - 1];
-            pB.SE = sR[s0][1][kk + 1]; pB.SW = sR[s0][1][kk - 1];
+            pA.E = sR[s1][0][t + 1]; pA.W = sR[s1][0][t - 1];
+            pA.N = sR[s2][0][t];     pA.S = sR[s0][0][t];
+            pA.NE = sR[s2][0][t + 1]; pA.NW = sR[s2][0][t - 1];
+            pA.SE = sR[s0][0][t + 1]; pA.SW = sR[s0][0][t - 1];
+            pB.E = sR[s1][1][t + 1]; pB.W = sR[s1][1][t - 1];
+            pB.N = sR[s2][1][t];     pB.S = sR[s0][1][t];
+            pB.NE = sR[s2][1][t + 1]; pB.NW = sR[s2][1][t - 1];
+            pB.SE = sR[s0][1][t + 1]; pB.SW = sR[s0][1][t - 1];
             collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
             store_site<T>(fout, g, y, x, cur, shift);
         }
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) cur[s][i] = nxt[s][i];
+    };
+    for (int y = y0; y < y1; y += 2) {
+        row(y, fa, fb);
+        if (y + 1 < y1) row(y + 1, fb, fa);
     }
 }
 
@@ -435,6 +652,7 @@ __global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, fl
 template <typename T>
 static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t st) {
     const Grid& g = L.grid;
+    (void)cudaGetLastError();   // a launch reports only its own error
     const int bx = (g.nx + kThreadsX - 1) / kThreadsX;
     if (kernel == LBM_KERNEL_TWO_PASS) {
         dim3 grid(bx, g.ny);
@@ -442,16 +660,31 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         collide_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, (T*)L.fout, g, L.phys, L.flag);
     } else if (kernel == LBM_KERNEL_STAGED) {
         const int ty = L.tile_y > 0 ? L.tile_y : 32;
-        const size_t smem = staged_smem_bytes<T>();
+        const size_t smem = block_smem_bytes<T>();
         static bool attr_set = false;   // one per instantiation
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(step_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        dim3 grid(bx, (g.ny + ty - 1) / ty);
-        step_staged_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
+        dim3 grid((g.nx + kOwned - 1) / kOwned, (g.ny + ty - 1) / ty);
+        step_block_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
+    } else if (kernel == LBM_KERNEL_WARP) {
+        const int ty = L.tile_y > 0 ? L.tile_y : default_tile_y();
+        const size_t smem = warp_kernel_smem_bytes<T>();
+        static bool attr_set = false;   // one per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(step_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        const int tiles_x = (g.nx + kWarpOwned - 1) / kWarpOwned;
+        const int tiles = tiles_x * ((g.ny + ty - 1) / ty);
+        const int blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        step_warp_kernel<T><<<blocks, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, tiles_x,
+                                                               tiles, L.flag);
     } else {
         const int ty = L.tile_y > 0 ? L.tile_y : 16;
         dim3 grid(bx, (g.ny + ty - 1) / ty);
@@ -470,6 +703,7 @@ cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st) {
 
 cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shift[2], const double* y0,
                         double mass_A, double mass_B, double minority, double width, cudaStream_t st) {
+    (void)cudaGetLastError();
     dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
     switch (storage) {
         case LBM_STORE_F16:

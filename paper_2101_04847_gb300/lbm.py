@@ -15,7 +15,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"fused": 0, "two_pass": 1, "staged": 2}
+KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3}
 
 
 class LbmParams(C.Structure):
@@ -69,6 +69,14 @@ _PROTOS = {
     "lbm_load": (C.c_int, [_h, C.c_char_p]),
     "lbm_destroy": (None, [_h]),
     "lbm_step_noalloc": (C.c_int, [_P(LbmParams), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_tune": (C.c_int, [_h, C.c_char_p, _P(C.c_int32), _P(C.c_double)]),
+    "lbm_ens_create": (C.c_int, [C.c_int32, _P(LbmParams), C.c_void_p, _P(C.c_void_p)]),
+    "lbm_ens_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_ens_sync": (C.c_int, [C.c_void_p]),
+    "lbm_ens_member": (C.c_int, [C.c_void_p, C.c_int32, _P(_h)]),
+    "lbm_ens_diagnostics": (C.c_int, [C.c_void_p, _P(LbmDiag)]),
+    "lbm_ens_tune": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_double)]),
+    "lbm_ens_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -238,3 +246,78 @@ class Solver:
 
     def load(self, path: str | Path):
         _check(self.lib.lbm_load(self._h, str(path).encode()), "lbm_load")
+
+    def tune(self, cache_path: str | Path | None = None) -> tuple[int, float]:
+        ty, ms = C.c_int32(), C.c_double()
+        _check(self.lib.lbm_tune(self._h, str(cache_path).encode() if cache_path else None,
+                                 C.byref(ty), C.byref(ms)), "lbm_tune")
+        self.params.tile_y = ty.value
+        return ty.value, ms.value
+
+
+class _Member(Solver):
+    """Borrowed view of an ensemble member (owned by the ensemble)."""
+
+    def __init__(self, lib, handle, params):   # noqa: D401 - no Solver.__init__
+        self.lib = lib
+        self._h = handle
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+
+    def close(self):
+        pass
+
+
+class Ensemble:
+    """Independent realisations advanced together by one launch per time step."""
+
+    def __init__(self, members: list[LbmParams], stream=None):
+        import torch
+
+        lib = load_library()
+        self.lib = lib
+        self.params = list(members)
+        arr = (LbmParams * len(members))(*members)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream or None
+        self._e = C.c_void_p()
+        _check(lib.lbm_ens_create(len(members), arr, C.c_void_p(stream) if stream else None, C.byref(self._e)),
+               "lbm_ens_create")
+        self.members = []
+        for i, p in enumerate(self.params):
+            h = C.c_void_p()
+            _check(lib.lbm_ens_member(self._e, i, C.byref(h)), "lbm_ens_member")
+            self.members.append(_Member(lib, h, p))
+
+    def step(self, n: int = 1):
+        _check(self.lib.lbm_ens_step(self._e, int(n)), "lbm_ens_step")
+
+    def sync(self):
+        _check(self.lib.lbm_ens_sync(self._e), "lbm_ens_sync")
+
+    def diagnostics(self) -> list[dict]:
+        out = (LbmDiag * len(self.params))()
+        _check(self.lib.lbm_ens_diagnostics(self._e, out), "lbm_ens_diagnostics")
+        return [diag_dict(d) for d in out]
+
+    def tune(self) -> tuple[int, float]:
+        ty, ms = C.c_int32(), C.c_double()
+        _check(self.lib.lbm_ens_tune(self._e, C.byref(ty), C.byref(ms)), "lbm_ens_tune")
+        return ty.value, ms.value
+
+    def close(self):
+        if getattr(self, "_e", None) and self._e.value:
+            self.lib.lbm_ens_destroy(self._e)
+            self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -43,7 +43,7 @@ def test_workspace_grows_with_the_grid(lib):
     small = lbm.workspace_bytes(lbm.default_params(nx=128, ny=256))
     big = lbm.workspace_bytes(lbm.default_params(nx=1024, ny=2048))
     assert small > 128 * 256 * 144
-    assert 40 < big / small < 70
+    assert 20 < big / small < 70
     half = lbm.workspace_bytes(lbm.default_params(nx=1024, ny=2048, storage="f16"))
     assert half < big
 
@@ -51,7 +51,7 @@ def test_workspace_grows_with_the_grid(lib):
 @pytest.mark.parametrize("field,value", [
     ("nx", 3), ("ny", 7), ("tau_A", 0.5), ("tau_B", 0.4), ("mass_A", 0.0), ("mass_B", -1.0),
     ("width", 0.0), ("minority", 1.0), ("n_modes", 65), ("crop_rows", 2), ("storage", 3),
-    ("kernel", 3), ("tile_y", -1), ("gravity_mode", 2), ("G", float("nan")), ("g", float("inf")),
+    ("kernel", 4), ("tile_y", -1), ("gravity_mode", 2), ("G", float("nan")), ("g", float("inf")),
 ])
 def test_invalid_parameters_are_rejected(lib, field, value):
     p = lbm.default_params()

@@ -1,0 +1,71 @@
+"""FP16 / BF16 shifted-population storage (populations stored as f - w_i rho0_s,
+FP32 collision) against the FP64 oracle and the FP32 path (GPU).
+
+The errors are reported (printed with -s) and bounded by the values measured on
+GB300, with margin; FP32 is the reference point of each comparison.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm_oracle as O
+from paper_2101_04847_gb300 import lbm
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 1000
+# max |drho_s| / max |rho_s| after 1000 steps of the 128 x 256 case, per storage.
+# Measured on GB300: f32 3.4e-6, f16 0.46, bf16 0.78.  The shift w_i rho0_s cannot
+# centre both phases (rho_A is ~1 in one bulk and ~0.08 in the other), and the
+# near-stationary bulk populations round the same way every step, so the 16-bit
+# round-off acts as a bias that moves the interface by cells within 1000 steps.
+DENSITY_BOUND = {"f32": 1e-5, "f16": 0.6, "bf16": 1.0}
+# relative error of E_p, h, L_int and of the masses after 1000 steps
+# (measured: f16 7e-3, 0.20, 0.0, 9e-4; bf16 3.6e-2, 0.32, 6e-3, 2.5e-2)
+DIAG_BOUND = {"f32": {"E_p": 1e-5, "h": 1e-4, "L_int": 1e-2, "mass_A": 1e-6, "mass_B": 1e-6},
+              "f16": {"E_p": 2e-2, "h": 0.4, "L_int": 5e-2, "mass_A": 3e-3, "mass_B": 3e-3},
+              "bf16": {"E_p": 0.1, "h": 0.6, "L_int": 5e-2, "mass_A": 6e-2, "mass_B": 6e-2}}
+# one step from the stored state: the output rounding of the 16-bit types
+ONE_STEP_BOUND = {"f16": 3e-4, "bf16": 2.5e-3}
+
+
+def oracle_params(d):
+    return O.Params(**{k: v for k, v in d.items() if k in O.Params.__dataclass_fields__})
+
+
+@pytest.fixture(scope="module")
+def reference():
+    d = inputs.params(inputs.C0, seed=1)
+    p = oracle_params(d)
+    f = O.step(O.initial_populations(p), p, STEPS)
+    return d, O.fields(f, p), O.diagnostics(f, p)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_storage_error_against_the_oracle(gpu, storage, reference):
+    d, ref, rdiag = reference
+    with lbm.Solver(kernel="staged", storage=storage, **d) as s:
+        s.step(STEPS)
+        got = s.fields()
+        diag = s.diagnostics()
+    errs = {k: float(np.max(np.abs(got[k] - ref[k])) / np.max(np.abs(ref[k]))) for k in ("rhoA", "rhoB")}
+    derr = {k: abs(diag[k] - rdiag[k]) / abs(rdiag[k]) for k in ("E_k", "E_p", "h", "L_int", "mass_A", "mass_B")}
+    print(f"\n{storage}: density {errs}  diagnostics {derr}")
+    assert max(errs.values()) <= DENSITY_BOUND[storage]
+    for k, bound in DIAG_BOUND[storage].items():
+        assert derr[k] <= bound, (k, derr[k])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("kernel", ["fused", "two_pass", "staged", "warp"])
+def test_one_step_of_the_16bit_storage(gpu, storage, kernel):
+    # the state the storage holds (rounded) is read back and stepped by the oracle
+    nx, ny = 150, 40
+    d = inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=3, g=1e-4)
+    with lbm.Solver(kernel=kernel, storage=storage, **d) as s:
+        s.set_populations(inputs.random_populations(9, nx, ny, lo=0.02, hi=0.2))
+        f = s.populations()
+        s.step(1)
+        got = s.populations()
+    ref = O.step(f, oracle_params(d), 1)
+    assert float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))) <= ONE_STEP_BOUND[storage]
