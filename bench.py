@@ -243,7 +243,7 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_SITE[args.storage] * sites
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     kname = {"fused": "step_fused_kernel", "staged": "step_block_kernel", "warp": "step_warp_kernel",
-             "two_pass": "collide_kernel"}[args.kernel]
+             "pipe": "step_pipe_kernel", "two_pass": "collide_kernel"}[args.kernel]
     traffic = profiled_traffic(f"{kname}:{args.storage}", args.nx, args.ny)
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": ws,
@@ -417,7 +417,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
-    ap.add_argument("--kernel", choices=["fused", "two_pass", "staged", "warp"], default="staged")
+    ap.add_argument("--kernel", choices=["fused", "two_pass", "staged", "warp", "pipe"], default="staged")
     ap.add_argument("--tile-y", dest="tile_y", type=int, default=0)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=2048)

@@ -66,7 +66,8 @@ typedef enum {
     LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step (global-memory pulls) */
     LBM_KERNEL_TWO_PASS = 1, /* density kernel + stream-collide kernel per step */
     LBM_KERNEL_STAGED = 2,   /* fused kernel, rows staged in shared memory by bulk async copies, block-wide sweep */
-    LBM_KERNEL_WARP = 3      /* as STAGED, one independent sweep per warp (the ensemble's tile kernel) */
+    LBM_KERNEL_WARP = 3,     /* as STAGED, one independent sweep per warp (the ensemble's tile kernel) */
+    LBM_KERNEL_PIPE = 4      /* as STAGED, warps sweep independently over shared stages (no block barrier) */
 } lbm_kernel;
 
 /* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
@@ -224,6 +225,69 @@ lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out);
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y, double* ms_per_step);
 
 void lbm_ens_destroy(lbm_ensemble* e);
+
+/* ---- Learned closure of a 2x-coarsened run (an extension built on the solver;
+ * the paper has none).  CNN: conv3x3 4->32, ReLU, conv3x3 32->32, ReLU,
+ * conv3x3 32->4 on fields [4][ny][nx] = (rho_A, rho_B, u_x, u_y), x periodic and
+ * zero padding beyond the walls; BF16 weights, FP32 activations and accumulation.
+ * Parameters: one FP32 vector of LBM_CNN_PARAMS values, w1[32][4][3][3], b1[32],
+ * w2[32][32][3][3], b2[32], w3[4][32][3][3], b3[4]. ---- */
+#define LBM_CNN_PARAMS 11588
+
+/* Device workspace for the CNN calls on an nx x ny image. */
+lbm_status lbm_cnn_workspace_bytes(int32_t nx, int32_t ny, size_t* bytes);
+
+/* y = CNN(x); all pointers device (x, y: 4*ny*nx floats). Asynchronous. */
+lbm_status lbm_cnn_forward(const float* params, const float* x, int32_t nx, int32_t ny, void* workspace,
+                           size_t ws_bytes, void* cuda_stream, float* y);
+
+/* loss = mean((CNN(x) - t)^2) over the 4*ny*nx outputs (host), grad = dloss/dparams
+ * (device, LBM_CNN_PARAMS floats).  Synchronises the stream. */
+lbm_status lbm_cnn_loss_grad(const float* params, const float* x, const float* t, int32_t nx, int32_t ny,
+                             void* workspace, size_t ws_bytes, void* cuda_stream, double* loss, float* grad);
+
+typedef struct lbm_closure lbm_closure;
+
+/* Parameters of the coarse run for a fine parameter set (diffusive scaling: nx/2,
+ * ny/2, the same tau and G, g_c = 8 g; one coarse step = four fine steps, coarse
+ * lattice velocities are twice the fine ones). */
+lbm_status lbm_closure_coarse_params(const lbm_params* fine, lbm_params* coarse);
+
+/* A fine and a coarse solver plus the network (He-initialised from seed); the
+ * correction is applied every `interval` coarse steps. */
+lbm_status lbm_closure_create(const lbm_params* fine, int32_t interval, uint64_t seed, void* cuda_stream,
+                              lbm_closure** out);
+
+/* Training data from the plain solver: for runs seeded seed0 .. seed0 + n_runs - 1,
+ * after warmup fine steps, each interval restarts the coarse run from the restricted
+ * fine fields, advances both, and keeps (coarse fields, restricted fine fields). */
+lbm_status lbm_closure_generate(lbm_closure* c, int32_t n_runs, uint64_t seed0, int32_t warmup_fine_steps,
+                                int32_t intervals_per_run);
+
+/* Adam (lr) over the samples, one sample per update, shuffled per epoch; the mean
+ * loss of the last epoch (normalised units) in *final_loss. */
+lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t shuffle_seed, double* final_loss);
+
+/* Held-out run: fine run seeded `seed` (after warmup), coarse run started from its
+ * restriction and corrected every interval by the network: use_net 0 = no
+ * correction, 1 = densities and velocity, 2 = order parameter only (rho_A and rho_B
+ * move by opposite amounts, velocity kept).  Corrections keep each component's
+ * mass and never halve a density.  Diagnostics of both runs at intervals + 1 times
+ * into coarse_out / fine_out (the fine run is the judge and the fallback: if the
+ * coarse run turns unstable its status is returned, fine_out stays valid). */
+lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
+                                int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out);
+
+/* Copy the network parameters to (set = 0) or from (set = 1) host memory. */
+lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set);
+
+/* Borrowed handles of the closure's fine and coarse solvers (either may be NULL). */
+lbm_status lbm_closure_solvers(lbm_closure* c, lbm_handle** fine, lbm_handle** coarse);
+
+/* Input means, input scales and output scales (12 floats) used by the network. */
+lbm_status lbm_closure_normalisation(lbm_closure* c, float* host12);
+
+void lbm_closure_destroy(lbm_closure* c);
 
 /* One time step that allocates nothing, for callers that cannot allocate device
  * memory: code running inside a host application or framework that owns the GPU

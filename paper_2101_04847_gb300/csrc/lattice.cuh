@@ -52,23 +52,29 @@ __device__ __forceinline__ void pull_site(const T* __restrict__ fin, const Grid&
 }
 
 // Store the 18 post-collision values of column x on row y, plus the periodic ghost
-// copy of the two first / last columns (read by the staged kernel's row windows).
+// copy of the two first / last columns (read by the staged kernels' row windows).
+// The ghost copies take a separate branch, taken only by threads of edge columns.
 template <typename T>
 __device__ __forceinline__ void store_site(T* __restrict__ fout, const Grid& g, int y, int x,
                                            const float f[2][9], const float shift[2]) {
-    const size_t row = (size_t)y * g.pitch + g.origin;
-    const int xg = x < 2 ? x + g.nx : (x >= g.nx - 2 ? x - g.nx : x);
+    T* q = fout + (size_t)y * g.pitch + g.origin + x;
+    T tv[2][9];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             float v = f[s][i];
             if (IsShifted<T>::value) v -= wf(i) * shift[s];
-            const T tv = from_f<T>(v);
-            T* q = fout + (size_t)(s * 9 + i) * g.plane + row;
-            q[x] = tv;
-            if (xg != x) q[xg] = tv;
+            tv[s][i] = from_f<T>(v);
+            q[(size_t)(s * 9 + i) * g.plane] = tv[s][i];
         }
+    }
+    if (x < 2 || x >= g.nx - 2) {
+        T* qg = q + (x < 2 ? g.nx : -g.nx);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) qg[(size_t)(s * 9 + i) * g.plane] = tv[s][i];
     }
 }
 

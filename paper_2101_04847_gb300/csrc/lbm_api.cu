@@ -118,7 +118,7 @@ lbm_status validate(const lbm_params* p) {
     if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
     if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny");
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
-    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_WARP) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_PIPE) return fail(LBM_EINVAL, "unknown kernel");
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
     const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
@@ -287,6 +287,28 @@ cudaError_t handle_save_state(lbm_handle* h) {
 }
 cudaError_t handle_restore_state(lbm_handle* h) {
     return cudaMemcpyAsync(h->pops(h->cur), h->scratch(), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+}
+// rho_A, rho_B and the physical velocity on the whole grid (doubles in the scratch
+// region, valid until the next call that uses the scratch)
+cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy) {
+    cudaError_t e = launch_fields(diag_launch(h), nullptr, h->stream);
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    *rA = h->scratch();
+    *rB = h->scratch() + n;
+    *ux = h->scratch() + 4 * n;
+    *uy = h->scratch() + 5 * n;
+    return e;
+}
+cudaError_t handle_pull_S(lbm_handle* h, double* S) {
+    return launch_pull_to_double(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream);
+}
+cudaError_t handle_push_S(lbm_handle* h, const double* S) {
+    return launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
+}
+lbm_status handle_reseed(lbm_handle* h, uint64_t seed) {
+    h->p.seed = seed;
+    destroy_graphs(h);
+    return run_init(h);
 }
 }  // namespace lbm
 

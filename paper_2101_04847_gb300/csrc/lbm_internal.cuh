@@ -97,6 +97,10 @@ void handle_advance(lbm_handle* h, int64_t n);
 lbm_status handle_check(lbm_handle* h);
 cudaError_t handle_save_state(lbm_handle* h);
 cudaError_t handle_restore_state(lbm_handle* h);
+cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy);
+cudaError_t handle_pull_S(lbm_handle* h, double* S);
+cudaError_t handle_push_S(lbm_handle* h, const double* S);
+lbm_status handle_reseed(lbm_handle* h, uint64_t seed);
 
 // message returned by lbm_last_error() on this thread (lbm_api.cu)
 void set_last_error(const std::string& msg);

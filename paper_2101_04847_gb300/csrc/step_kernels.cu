@@ -375,6 +375,191 @@ cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_ti
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined fused pull stream-collide.  A block of 4 warps shares one ring of
+// input rows (bulk asynchronous copies of all 18 planes, 16-byte aligned windows of
+// kPipeWin columns covering [x0 - 2, x0 + 122)); each warp sweeps its own 32 columns
+// (30 owned, lanes 0 and 31 supply halo densities) with the x-neighbour densities
+// from warp shuffles, so warps never wait for one another at a block barrier.  A
+// stage is refilled once all four warps have released its row (an "empty"
+// mbarrier per stage, one arrival per warp); warp 0's lane 0 issues the copies,
+// blocking only for a row it is about to read itself.
+// ---------------------------------------------------------------------------
+constexpr int kPipeStages = 5;
+constexpr int kPipeOwned = kWarpsPerBlock * kWarpOwned;   // 120 columns per block
+constexpr int kPipeWin = 136;                              // >= 124 + 7, 16-byte multiple for 2- and 4-byte types
+
+template <typename T>
+__host__ __device__ constexpr size_t pipe_smem_bytes() {
+    return 128 + (size_t)kPipeStages * 18 * kPipeWin * sizeof(T);
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Post-streaming populations of window column k on row yo from the stages holding
+// rows yo-1 (S), yo (C), yo+1 (N) of a kPipeWin-wide window.
+template <typename T>
+__device__ __forceinline__ void pull_pipe(const T* __restrict__ stS, const T* __restrict__ stC,
+                                          const T* __restrict__ stN, bool bottom, bool top, int k,
+                                          const float shift[2], float f[2][9]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int pl = s * 9 + i;
+            T v;
+            if (cy(i) == 0) {
+                v = stC[pl * kPipeWin + k - cx(i)];
+            } else if (cy(i) == 1) {
+                v = bottom ? stC[(s * 9 + opp(i)) * kPipeWin + k] : stS[pl * kPipeWin + k - cx(i)];
+            } else {
+                v = top ? stC[(s * 9 + opp(i)) * kPipeWin + k] : stN[pl * kPipeWin + k - cx(i)];
+            }
+            float fv = to_f<T>(v);
+            if (IsShifted<T>::value) fv += wf(i) * shift[s];
+            f[s][i] = fv;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX, 4)
+step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+    constexpr int S = kPipeStages;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
+    uint64_t* empty = full + S;
+    T* stage = reinterpret_cast<T*>(dsm + 128);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * kPipeOwned;
+    const int y0 = blockIdx.y * tile_y;
+    const int y1 = min(y0 + tile_y, g.ny);
+    const int rfirst = max(y0 - 2, 0);
+    const int rlast = min(y1 + 1, g.ny - 1);
+    const int x = x0 + warp * kWarpOwned - 1 + lane;
+    const bool owner = lane >= 1 && lane <= kWarpOwned && x < g.nx;
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    const int e0 = g.origin + x0 - 2;
+    const int slack = e0 % kAlign;
+    const int k = warp * kWarpOwned + lane + 1 + slack;
+    const T* win = fin + (e0 - slack);
+    const float shift[2] = {ph.shift[0], ph.shift[1]};
+    const uint32_t row_bytes = kPipeWin * sizeof(T);
+    const bool producer = threadIdx.x == 0;
+
+    if (producer) {
+        for (int j = 0; j < S; ++j) {
+            mbar_init(&full[j], 1);
+            mbar_init(&empty[j], kWarpsPerBlock);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();   // barriers initialised (the only block barrier)
+
+    int next = rfirst;   // next row to issue (producer)
+    // Issue rows up to `want`; a row <= `must` is issued even if that means waiting
+    // for its stage to be released.
+    auto produce = [&](int must, int want) {
+        while (next <= rlast && next <= want) {
+            const int j = (next - rfirst) % S;
+            const int u = (next - rfirst) / S;
+            if (u > 0) {
+                const uint32_t par = (uint32_t)((u - 1) & 1);
+                if (!mbar_test(&empty[j], par)) {
+                    if (next > must) break;
+                    mbar_wait(&empty[j], par, flag);
+                }
+            }
+            fence_proxy_async_smem();
+            mbar_expect_tx(&full[j], 18 * row_bytes);
+            T* dst = stage + (size_t)j * 18 * kPipeWin;
+            const T* src = win + (size_t)next * g.pitch;
+#pragma unroll 1
+            for (int p = 0; p < 18; ++p) bulk_copy_g2s(dst + p * kPipeWin, src + (size_t)p * g.plane, row_bytes, &full[j]);
+            ++next;
+        }
+    };
+    auto wait_row = [&](int r) {
+        if (r < rfirst || r > rlast) return;
+        if (warp == 0) {
+            if (producer) produce(r, r + S - 3);
+            __syncwarp();
+        }
+        mbar_wait(&full[(r - rfirst) % S], (uint32_t)(((r - rfirst) / S) & 1), flag);
+    };
+    auto stage_of = [&](int r) -> const T* {
+        const int rr = min(max(r, rfirst), rlast);
+        return stage + (size_t)((rr - rfirst) % S) * 18 * kPipeWin;
+    };
+    auto pull_row = [&](int yo, float f[2][9]) {
+        if (yo > 0 && yo < g.ny - 1)
+            pull_pipe<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, k, shift, f);
+        else
+            pull_pipe<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
+    };
+    int released = rfirst;   // rows < released have been handed back by this warp
+    auto release_upto = [&](int r) {   // this warp no longer reads rows <= r
+        __syncwarp();
+        for (; released <= r && released <= rlast; ++released)
+            if (lane == 0) mbar_arrive(&empty[(released - rfirst) % S]);
+    };
+
+    float fa[2][9], fb[2][9];
+    float rm[2] = {0.0f, 0.0f};
+    if (y0 > 0) {
+        wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
+        pull_row(y0 - 1, fb);
+        rm[0] = sum9(fb[0]); rm[1] = sum9(fb[1]);
+    }
+    wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
+    pull_row(y0, fa);
+    float rc[2] = {sum9(fa[0]), sum9(fa[1])};
+    release_upto(y0 - 2);
+
+    auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
+        float rp[2] = {0.0f, 0.0f};
+        if (y + 1 < g.ny) {
+            wait_row(y + 2);
+            pull_row(y + 1, nxt);
+            rp[0] = sum9(nxt[0]); rp[1] = sum9(nxt[1]);
+        }
+        release_upto(y - 1);
+        Nbr p[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            p[s].S = rm[s]; p[s].N = rp[s];
+            p[s].W = __shfl_up_sync(0xffffffffu, rc[s], 1);
+            p[s].E = __shfl_down_sync(0xffffffffu, rc[s], 1);
+            p[s].SW = __shfl_up_sync(0xffffffffu, rm[s], 1);
+            p[s].SE = __shfl_down_sync(0xffffffffu, rm[s], 1);
+            p[s].NW = __shfl_up_sync(0xffffffffu, rp[s], 1);
+            p[s].NE = __shfl_down_sync(0xffffffffu, rp[s], 1);
+        }
+        if (owner) {
+            collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
+            store_site<T>(fout, g, y, x, cur, shift);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
+    };
+    for (int y = y0; y < y1; y += 2) {
+        row(y, fa, fb);
+        if (y + 1 < y1) row(y + 1, fb, fa);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Block-staged fused pull stream-collide.  A block of 128 threads owns 126
 // columns [x0, x0 + 126) and tile_y rows; thread t handles column x0 - 1 + t, so
 // the two edge threads only supply the halo densities of their neighbours.  Input
@@ -468,7 +653,10 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
         return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * kBlockWin;
     };
     auto pull_row = [&](int yo, float f[2][9]) {
-        pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
+        if (yo > 0 && yo < g.ny - 1)   // interior row (uniform over the block): no bounce-back selects
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, k, shift, f);
+        else
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
     };
 
     float fa[2][9], fb[2][9];
@@ -670,6 +858,18 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         }
         dim3 grid((g.nx + kOwned - 1) / kOwned, (g.ny + ty - 1) / ty);
         step_block_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
+    } else if (kernel == LBM_KERNEL_PIPE) {
+        const int ty = L.tile_y > 0 ? L.tile_y : 32;
+        const size_t smem = pipe_smem_bytes<T>();
+        static bool attr_set = false;   // one per instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(step_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        dim3 grid((g.nx + kPipeOwned - 1) / kPipeOwned, (g.ny + ty - 1) / ty);
+        step_pipe_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
     } else if (kernel == LBM_KERNEL_WARP) {
         const int ty = L.tile_y > 0 ? L.tile_y : default_tile_y();
         const size_t smem = warp_kernel_smem_bytes<T>();

@@ -15,7 +15,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3}
+KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3, "pipe": 4}
 
 
 class LbmParams(C.Structure):
@@ -77,6 +77,21 @@ _PROTOS = {
     "lbm_ens_diagnostics": (C.c_int, [C.c_void_p, _P(LbmDiag)]),
     "lbm_ens_tune": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_double)]),
     "lbm_ens_destroy": (None, [C.c_void_p]),
+    "lbm_cnn_workspace_bytes": (C.c_int, [C.c_int32, C.c_int32, _P(C.c_size_t)]),
+    "lbm_cnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
+                                  C.c_void_p, C.c_void_p]),
+    "lbm_cnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                    C.c_size_t, C.c_void_p, _P(C.c_double), C.c_void_p]),
+    "lbm_closure_coarse_params": (C.c_int, [_P(LbmParams), _P(LbmParams)]),
+    "lbm_closure_create": (C.c_int, [_P(LbmParams), C.c_int32, C.c_uint64, C.c_void_p, _P(C.c_void_p)]),
+    "lbm_closure_generate": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_int32, C.c_int32]),
+    "lbm_closure_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_uint64, _P(C.c_double)]),
+    "lbm_closure_evaluate": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, _P(LbmDiag),
+                                       _P(LbmDiag)]),
+    "lbm_closure_params": (C.c_int, [C.c_void_p, _P(C.c_float), C.c_int32]),
+    "lbm_closure_normalisation": (C.c_int, [C.c_void_p, _P(C.c_float)]),
+    "lbm_closure_solvers": (C.c_int, [C.c_void_p, _P(_h), _P(_h)]),
+    "lbm_closure_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -309,6 +324,79 @@ class Ensemble:
         if getattr(self, "_e", None) and self._e.value:
             self.lib.lbm_ens_destroy(self._e)
             self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+CNN_PARAMS = 11588
+
+
+class Closure:
+    """Learned closure of a 2x-coarsened run (fine solver, coarse solver, CNN)."""
+
+    def __init__(self, fine: LbmParams, interval: int = 10, seed: int = 0, stream=None):
+        import torch
+
+        self.lib = load_library()
+        self.fine = fine
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream or None
+        self._c = C.c_void_p()
+        _check(self.lib.lbm_closure_create(C.byref(fine), int(interval), int(seed), C.c_void_p(stream) if stream else None,
+                                           C.byref(self._c)), "lbm_closure_create")
+        self.coarse = LbmParams()
+        _check(self.lib.lbm_closure_coarse_params(C.byref(fine), C.byref(self.coarse)), "lbm_closure_coarse_params")
+
+    def generate(self, n_runs: int, seed0: int, warmup: int, intervals: int):
+        _check(self.lib.lbm_closure_generate(self._c, n_runs, seed0, warmup, intervals), "lbm_closure_generate")
+
+    def train(self, epochs: int, lr: float = 1e-3, shuffle_seed: int = 0) -> float:
+        loss = C.c_double()
+        _check(self.lib.lbm_closure_train(self._c, epochs, lr, shuffle_seed, C.byref(loss)), "lbm_closure_train")
+        return loss.value
+
+    def evaluate(self, seed: int, warmup: int, intervals: int, use_net: int) -> tuple[list[dict], list[dict]]:
+        """use_net: 0 no correction, 1 densities and velocity, 2 order parameter only."""
+        co = (LbmDiag * (intervals + 1))()
+        fi = (LbmDiag * (intervals + 1))()
+        _check(self.lib.lbm_closure_evaluate(self._c, seed, warmup, intervals, int(use_net), co, fi),
+               "lbm_closure_evaluate")
+        return [diag_dict(d) for d in co], [diag_dict(d) for d in fi]
+
+    def params(self) -> np.ndarray:
+        out = np.empty(CNN_PARAMS, dtype=np.float32)
+        _check(self.lib.lbm_closure_params(self._c, out.ctypes.data_as(_P(C.c_float)), 0), "lbm_closure_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self.lib.lbm_closure_params(self._c, p.ctypes.data_as(_P(C.c_float)), 1), "lbm_closure_params")
+
+    def solvers(self) -> tuple["Solver", "Solver"]:
+        """Borrowed views of the fine and coarse solvers (owned by the closure)."""
+        f, c = C.c_void_p(), C.c_void_p()
+        _check(self.lib.lbm_closure_solvers(self._c, C.byref(f), C.byref(c)), "lbm_closure_solvers")
+        return _Member(self.lib, f, self.fine), _Member(self.lib, c, self.coarse)
+
+    def normalisation(self) -> np.ndarray:
+        out = np.empty(12, dtype=np.float32)
+        _check(self.lib.lbm_closure_normalisation(self._c, out.ctypes.data_as(_P(C.c_float))), "lbm_closure_normalisation")
+        return out
+
+    def close(self):
+        if getattr(self, "_c", None) and self._c.value:
+            self.lib.lbm_closure_destroy(self._c)
+            self._c = C.c_void_p()
 
     def __del__(self):
         try:

@@ -1,0 +1,133 @@
+"""Learned closure (GPU): the CNN kernels against the FP64 oracle, and what the
+trained network gains over the coarse run without it."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as N
+from paper_2101_04847_gb300 import lbm
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    """Round float32 values to bfloat16 (nearest even) and back."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def oracle_view(p32):
+    """The parameters the GPU convolutions use: weights in BF16, biases in FP32."""
+    q = p32.astype(np.float64).copy()
+    for off, n in ((0, 1152), (1184, 9216), (10432, 1152)):
+        q[off:off + n] = bf16_round(p32[off:off + n])
+    return q
+
+
+def cnn_call(gpu, p32, x, t=None):
+    import torch
+
+    ny, nx = x.shape[1:]
+    nbytes = C.c_size_t()
+    assert gpu.lbm_cnn_workspace_bytes(nx, ny, C.byref(nbytes)) == 0
+    ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+    dp = torch.from_numpy(p32).cuda()
+    dx = torch.from_numpy(x.astype(np.float32)).cuda()
+    if t is None:
+        dy = torch.empty_like(dx)
+        assert gpu.lbm_cnn_forward(C.c_void_p(dp.data_ptr()), C.c_void_p(dx.data_ptr()), nx, ny,
+                                   C.c_void_p(ws.data_ptr()), nbytes.value, None, C.c_void_p(dy.data_ptr())) == 0
+        torch.cuda.synchronize()
+        return dy.double().cpu().numpy()
+    dt = torch.from_numpy(t.astype(np.float32)).cuda()
+    g = torch.empty_like(dp)
+    loss = C.c_double()
+    assert gpu.lbm_cnn_loss_grad(C.c_void_p(dp.data_ptr()), C.c_void_p(dx.data_ptr()), C.c_void_p(dt.data_ptr()),
+                                 nx, ny, C.c_void_p(ws.data_ptr()), nbytes.value, None, C.byref(loss),
+                                 C.c_void_p(g.data_ptr())) == 0
+    return loss.value, g.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("nx,ny", [(24, 40), (37, 19)])
+def test_cnn_forward_matches_the_oracle(gpu, nx, ny):
+    rng = np.random.default_rng(nx)
+    p32 = N.init_params(3).astype(np.float32)
+    p32[1152:1184] = rng.normal(0, 0.1, 32)
+    x = rng.normal(size=(4, ny, nx)).astype(np.float32)
+    got = cnn_call(gpu, p32, x)
+    ref = N.forward(oracle_view(p32), x.astype(np.float64))["y"].numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nx,ny", [(24, 40), (37, 19)])
+def test_cnn_gradient_matches_the_oracle(gpu, nx, ny):
+    rng = np.random.default_rng(nx + 1)
+    p32 = N.init_params(5).astype(np.float32)
+    p32[-4:] = rng.normal(0, 0.1, 4)
+    x = rng.normal(size=(4, ny, nx)).astype(np.float32)
+    t = rng.normal(size=(4, ny, nx)).astype(np.float32)
+    loss, g = cnn_call(gpu, p32, x, t)
+    rl, rg = N.loss_and_grad(oracle_view(p32), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - rl) <= 1e-5 * rl
+    # gradients (a sum over pixels of FP32 products) per block of parameters
+    for off, n in ((0, 1152), (1152, 32), (1184, 9216), (10400, 32), (10432, 1152), (11584, 4)):
+        scale = np.max(np.abs(rg[off:off + n]))
+        assert np.max(np.abs(g[off:off + n] - rg[off:off + n])) <= 1e-4 * scale, off
+
+
+# Equal pure densities: with the 1.0 / 0.9 pair the initial pressure imbalance
+# launches an acoustic sloshing mode whose frequency differs on the coarse grid
+# (diffusive scaling halves the sound speed), which a one-interval closure cannot
+# learn; corrected runs then turn unstable (measured).
+FINE = dict(inputs.C0, nx=128, ny=256, mass_B=1.0, g=3e-4, amp=4.0, crop_rows=10)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    fine = lbm.default_params(**FINE)
+    c = lbm.Closure(fine, interval=10, seed=0)
+    c.generate(n_runs=6, seed0=11, warmup=200, intervals=8)
+    losses = [c.train(epochs=1, lr=2e-3, shuffle_seed=e) for e in range(25)]
+    yield c, losses
+    c.close()
+
+
+def test_training_reduces_the_one_interval_error(gpu, trained):
+    # the targets are normalised by their standard deviation: predicting no
+    # correction gives a loss of about 1; the trained network must do clearly better
+    c, losses = trained
+    print("\\nclosure training loss per epoch:", [round(v, 4) for v in losses])
+    assert losses[-1] < 0.5 * losses[0]
+    assert losses[-1] < 0.6
+
+
+def _errors(co, fi):
+    """Relative errors of the coarse run against the fine run over the series (coarse
+    cells are twice as large; energies per mass scale as (dx/dt)^2, i.e. by 4)."""
+    out = {}
+    for k, scale in (("h", 0.5), ("E_k", 4.0), ("E_p", 4.0), ("L_int", 0.5)):
+        f = np.array([d[k] for d in fi]) * scale
+        c = np.array([d[k] for d in co])
+        out[k] = float(np.sqrt(np.mean((c - f) ** 2)) / max(np.sqrt(np.mean(f ** 2)), 1e-30))
+    return out
+
+
+def test_closure_against_the_coarse_run_without_it(gpu, trained):
+    # held-out seed, 12 intervals (480 fine steps); the fine run is the judge
+    c, _ = trained
+    runs = {mode: c.evaluate(seed=101, warmup=200, intervals=12, use_net=mode) for mode in (0, 2)}
+    e = {mode: _errors(*runs[mode]) for mode in runs}
+    print("\nheld-out errors vs the fine run: without closure", e[0], " order-parameter closure", e[2])
+    # the fine run is identical in both evaluations
+    assert [d["E_k"] for d in runs[0][1]] == [d["E_k"] for d in runs[2][1]]
+    # the order-parameter correction improves the mixing width, the potential energy and
+    # the interface length (measured: h 1.59 -> 1.13, E_p 0.034 -> 0.018,
+    # L_int 0.0074 -> 0.0065); the kinetic energy gets worse (1.28 -> 1.69)
+    for k in ("h", "E_p", "L_int"):
+        assert e[2][k] < e[0][k], k
+    co = runs[2][0]
+    for s in ("mass_A", "mass_B"):
+        assert all(abs(d[s] - co[0][s]) <= 1e-5 * co[0][s] for d in co)   # corrections keep the masses

@@ -38,7 +38,9 @@ def test_ensemble_members_equal_solo_runs(gpu):
         with lbm.Solver(member_params(m, tile_y=16)) as s:
             s.step(73)
             want = s.populations()
-        assert float(np.max(np.abs(g - want)) / np.max(np.abs(want))) < 1e-6, m
+        # one unit in the last place of the storage type
+        tol = {"f32": 1e-6, "f16": 2e-3, "bf16": 1.6e-2}[m["storage"]]
+        assert float(np.max(np.abs(g - want)) / np.max(np.abs(want))) < tol, m
         assert d["step"] == 73
 
 
@@ -81,4 +83,4 @@ def test_tune_keeps_state_and_caches(gpu, tmp_path):
     assert int(text[1]) == ty
     with lbm.Solver(kernel="staged", **d) as s2:
         ty2, ms2 = s2.tune(cache)                                      # found in the cache, not re-timed
-        assert (ty2, ms2) == (ty, pytest.approx(ms, rel=1e-5))
+        assert ty2 == ty and ms2 == pytest.approx(ms, rel=1e-3)   # stored with 6 decimals
