@@ -14,19 +14,33 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
     sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
 }
 
-// Error-free transformations (Knuth's TwoSum) used to repair the FP32 rounding of
-// mass and momentum; sums are taken as balanced trees of double-float values,
-// which keeps the dependency chains short.
+// Error-free transformations used to repair the FP32 rounding of mass and
+// momentum: Knuth's TwoSum (any operands) and Dekker's Fast2Sum (exact when the
+// running sum is at least as large as the addend, as for sums of non-negative
+// populations started from the largest term).
 struct DF { float hi, lo; };
 __device__ __forceinline__ DF df_two(float a, float b) {
     const float s = a + b;
     const float bb = s - a;
     return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ DF df_plus(DF a, DF b) {
-    DF s = df_two(a.hi, b.hi);
-    s.lo += a.lo + b.lo;
+__device__ __forceinline__ void df_fast_add(DF& d, float v) {
+    const float s = d.hi + v;
+    d.lo += v - (s - d.hi);
+    d.hi = s;
+}
+// a - b for two double-float values
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+    DF s = df_two(a.hi, -b.hi);
+    s.lo += a.lo - b.lo;
     return s;
+}
+// f[a] + f[b] + f[c] (non-negative, |f[a]| largest) in double-float
+__device__ __forceinline__ DF df_sum3(float a, float b, float c) {
+    DF d = {a, 0.0f};
+    df_fast_add(d, b);
+    df_fast_add(d, c);
+    return d;
 }
 
 // Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
@@ -36,7 +50,8 @@ __device__ __forceinline__ DF df_plus(DF a, DF b) {
 // - 3/2 u'^2) and f^eq_i - f^eq_ibar = 6 w rho c.u'.
 //
 // kExact (FP32 storage): each component's momentum after the update is summed in
-// double-float and nudged, on the pairs 1/3 and 2/4, to (1 - w) j_s + w rho_s u'_s;
+// double-float (positive and negative directions separately, then their
+// difference) and nudged, on the pairs 1/3 and 2/4, to (1 - w) j_s + w rho_s u'_s;
 // the rest population is then set to rho_s - sum_{i>0} f*_i with both sums in
 // double-float.  Both are identities of the exact BGK update (it keeps rho_s and gives
 // that momentum); in FP32 they remove the per-site rounding of mass and of the
@@ -50,9 +65,9 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (kExact) {
-            const DF a = df_plus(df_two(f[s][0], f[s][1]), df_two(f[s][2], f[s][3]));
-            const DF b = df_plus(df_two(f[s][4], f[s][5]), df_two(f[s][6], f[s][7]));
-            rr[s] = df_plus(df_plus(a, b), DF{f[s][8], 0.0f});
+            rr[s] = {f[s][0], 0.0f};   // rest population first: the largest term
+#pragma unroll
+            for (int i = 1; i < 9; ++i) df_fast_add(rr[s], f[s][i]);
         } else {
             rr[s] = {sum9(f[s]), 0.0f};
         }
@@ -105,8 +120,7 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
             // x: target (1 - w) jx + w rho vx, repaired on the pair 1 / 3
             {
                 const float t = fmaf(om1, jx[s], om * (rho[s] * vx));
-                const DF o = df_plus(df_plus(df_two(f[s][1], -f[s][3]), df_two(f[s][5], -f[s][7])),
-                                     df_two(f[s][8], -f[s][6]));
+                const DF o = df_sub(df_sum3(f[s][1], f[s][5], f[s][8]), df_sum3(f[s][3], f[s][7], f[s][6]));
                 const float half = 0.5f * ((t - o.hi) - o.lo);
                 f[s][1] += half;
                 f[s][3] -= half;
@@ -114,14 +128,14 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
             // y: pair 2 / 4
             {
                 const float t = fmaf(om1, jy[s], om * (rho[s] * vy));
-                const DF o = df_plus(df_plus(df_two(f[s][2], -f[s][4]), df_two(f[s][5], -f[s][7])),
-                                     df_two(f[s][6], -f[s][8]));
+                const DF o = df_sub(df_sum3(f[s][2], f[s][5], f[s][6]), df_sum3(f[s][4], f[s][7], f[s][8]));
                 const float half = 0.5f * ((t - o.hi) - o.lo);
                 f[s][2] += half;
                 f[s][4] -= half;
             }
-            const DF m = df_plus(df_plus(df_two(f[s][1], f[s][2]), df_two(f[s][3], f[s][4])),
-                                 df_plus(df_two(f[s][5], f[s][6]), df_two(f[s][7], f[s][8])));
+            DF m = {f[s][1], 0.0f};    // axis directions (weight 1/9) before the diagonals
+#pragma unroll
+            for (int i = 2; i < 9; ++i) df_fast_add(m, f[s][i]);
             f[s][0] = (rr[s].hi - m.hi) + (rr[s].lo - m.lo);
         }
     }

@@ -571,7 +571,7 @@ step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
 // densities of three rows are exchanged through a shared-memory ring (one block
 // barrier per row).
 // ---------------------------------------------------------------------------
-constexpr int kBlockStages = 5;
+constexpr int kBlockStages = 5;   // rows y..y+2 in use + 2 rows prefetched (4 stages / 5 blocks per SM measured slower)
 constexpr int kOwned = kThreadsX - 2;
 constexpr int kBlockWin = 144;   // >= 128 + 2 + 7 (alignment slack), 16-byte multiple for 2- and 4-byte types
 
@@ -674,6 +674,12 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
     pull_row(y0, fa);
     sR[y0 & 3][0][t] = sum9(fa[0]);
     sR[y0 & 3][1][t] = sum9(fa[1]);
+    // everybody is past the prologue's reads of row y0 - 2: its stage can take row y0 + 2
+    __syncthreads();
+    if (t == 0) {
+        fence_proxy_async_smem();
+        for (; next <= rlast && next - kBlockStages <= y0 - 2; ++next) issue(next);
+    }
 
     auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
         const int sn = (y + 1) & 3;

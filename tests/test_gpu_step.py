@@ -13,7 +13,7 @@ from tests import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["fused", "two_pass", "staged", "warp"]
+KERNELS = ["fused", "two_pass", "staged", "warp", "pipe"]
 
 
 def oracle_params(d):
@@ -118,7 +118,7 @@ def test_graph_replay_equals_single_launches(gpu):
         assert np.array_equal(a.populations(), b.populations())
 
 
-@pytest.mark.parametrize("other", ["two_pass", "staged", "warp"])
+@pytest.mark.parametrize("other", ["two_pass", "staged", "warp", "pipe"])
 def test_kernels_agree(gpu, other):
     # same per-site arithmetic; only the compiler's contraction choices may differ
     d = inputs.params(inputs.C0, nx=200, ny=96)
@@ -128,7 +128,7 @@ def test_kernels_agree(gpu, other):
         assert rel_err(a.populations(), b.populations()) < 1e-6
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged", "warp"])
+@pytest.mark.parametrize("kernel", ["fused", "staged", "warp", "pipe"])
 @pytest.mark.parametrize("tile_y", [1, 5, 16, 64, 300])
 def test_tile_shape_does_not_change_the_result(gpu, kernel, tile_y):
     d = inputs.params(inputs.C0, nx=140, ny=150)
@@ -138,7 +138,7 @@ def test_tile_shape_does_not_change_the_result(gpu, kernel, tile_y):
         assert np.array_equal(a.populations(), b.populations())
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged", "warp"])
+@pytest.mark.parametrize("kernel", ["fused", "staged", "warp", "pipe"])
 def test_bench_configuration_one_step_full_grid(gpu, kernel):
     # 1024 x 2048 in the launch configurations the benchmark times (default tiles)
     d = inputs.params(inputs.C1, seed=2)
