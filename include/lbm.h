@@ -90,7 +90,9 @@ typedef struct {
     int32_t crop_rows;       /* rows cut at top and bottom for averages, >= 3, 2*crop_rows < ny */
     int32_t storage;         /* lbm_storage */
     int32_t kernel;          /* lbm_kernel */
-    int32_t tile_y;          /* rows per block of the fused kernel; 0 = default */
+    int32_t tile_y;          /* at most this many rows per block tile of the step kernel (the
+                              * rows are split evenly over the tiles); 0 = the kernel's default
+                              * (block-staged: one wave of tiles filling every SM) */
     double shift_A, shift_B; /* rho0_s of the shifted storage; <= 0 means (mass_s (1 + minority)) / 2 */
 } lbm_params;
 
@@ -191,7 +193,7 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 void lbm_destroy(lbm_handle* h);
 
 /* Pick the rows per tile (tile_y) of the handle's step kernel by timing candidate
- * values on the handle's own grid, then use the fastest.  The state and the step
+ * values (0 = the default among them) on the handle's own grid, then use the fastest.  The state and the step
  * counter are left as they were.  cache_path: NULL, or a text file of
  * "<gpu>|<kernel>|<storage>|<nx>x<ny> <tile_y> <ms>" lines; a matching line is used
  * without timing, a new result is appended.  Outputs may be NULL. */

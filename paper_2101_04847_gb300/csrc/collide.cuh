@@ -14,68 +14,34 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
     sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
 }
 
-// Error-free transformations used to repair the FP32 rounding of mass and
-// momentum: Knuth's TwoSum (any operands) and Dekker's Fast2Sum (exact when the
-// running sum is at least as large as the addend, as for sums of non-negative
-// populations started from the largest term).
-struct DF { float hi, lo; };
-__device__ __forceinline__ DF df_two(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ void df_fast_add(DF& d, float v) {
-    const float s = d.hi + v;
-    d.lo += v - (s - d.hi);
-    d.hi = s;
-}
-// a - b for two double-float values
-__device__ __forceinline__ DF df_sub(DF a, DF b) {
-    DF s = df_two(a.hi, -b.hi);
-    s.lo += a.lo - b.lo;
-    return s;
-}
-// f[a] + f[b] + f[c] (non-negative, |f[a]| largest) in double-float
-__device__ __forceinline__ DF df_sum3(float a, float b, float c) {
-    DF d = {a, 0.0f};
-    df_fast_add(d, b);
-    df_fast_add(d, c);
-    return d;
-}
-
 // Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
 // "Equilibrium distribution"): f <- f + (f^eq(rho_s, u + tau_s a_s) - f) / tau_s with
 // a_s = F_s / rho_s computed directly (no division by rho_s).  The equilibrium is
 // evaluated per pair of opposite directions: f^eq_i + f^eq_ibar = 2 w rho (1 + 9/2 (c.u')^2
 // - 3/2 u'^2) and f^eq_i - f^eq_ibar = 6 w rho c.u'.
 //
-// kExact (FP32 storage): each component's momentum after the update is summed in
-// double-float (positive and negative directions separately, then their
-// difference) and nudged, on the pairs 1/3 and 2/4, to (1 - w) j_s + w rho_s u'_s;
-// the rest population is then set to rho_s - sum_{i>0} f*_i with both sums in
-// double-float.  Both are identities of the exact BGK update (it keeps rho_s and gives
-// that momentum); in FP32 they remove the per-site rounding of mass and of the
-// large, nearly cancelling inter-component Shan-Chen momenta, which otherwise
-// random-walks the interface (~1e-5 of rho after 1000 steps at tau = 1).
+// kExact (FP32 storage) works with the increments d_i = f*_i - f_i that the stored
+// values really received (d_i is recomputed from the rounded f*_i; the subtraction
+// is exact while |d_i| <= |f_i|, as in Dekker's Fast2Sum).  The BGK update changes a
+// component's momentum by omega (rho_s u'_s - j_s) and its mass by nothing; the
+// pairs 1/3 and 2/4 take half of the momentum defect each way, and the rest
+// population takes minus the sum of the other eight increments.  The defects are
+// sums of small increments, so their rounding is far below one unit in the last
+// place of a population: mass is kept up to one rounding of f*_0 and the large,
+// nearly cancelling inter-component Shan-Chen momenta do not random-walk the
+// interface (plain FP32 moves rho by ~1e-5 of its range in 1000 steps at tau = 1).
 template <bool kExact>
 __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, const Nbr& psiB,
                                              const Physics& ph, int y, int ny, int* flag) {
-    DF rr[2];
-    float jx[2], jy[2];
+    float rho[2], jx[2], jy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        if (kExact) {
-            rr[s] = {f[s][0], 0.0f};   // rest population first: the largest term
-#pragma unroll
-            for (int i = 1; i < 9; ++i) df_fast_add(rr[s], f[s][i]);
-        } else {
-            rr[s] = {sum9(f[s]), 0.0f};
-        }
+        rho[s] = sum9(f[s]);
         jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
         jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][7]) + (f[s][6] - f[s][8]);
     }
-    const float rA = rr[0].hi + rr[0].lo;
-    const float rB = rr[1].hi + rr[1].lo;
+    const float rA = rho[0];
+    const float rB = rho[1];
     if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
     const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
     const float ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
@@ -90,7 +56,6 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
     ay[1] = -ph.G * nAy + ph.ay_ext[1];
     if (y == 0) { ay[0] += ph.ay_wall_bottom[0]; ay[1] += ph.ay_wall_bottom[1]; }
     if (y == ny - 1) { ay[0] += ph.ay_wall_top[0]; ay[1] += ph.ay_wall_top[1]; }
-    const float rho[2] = {rA, rB};
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const float vx = ux + ph.tau[s] * ax[s];
@@ -113,31 +78,32 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
                 feq[b[q]] = sym - anti;
             }
         }
+        if (!kExact) {
 #pragma unroll
-        for (int i = kExact ? 1 : 0; i < 9; ++i) f[s][i] = fmaf(om, feq[i] - f[s][i], f[s][i]);
-        if (kExact) {
-            const float om1 = 1.0f - om;
-            // x: target (1 - w) jx + w rho vx, repaired on the pair 1 / 3
-            {
-                const float t = fmaf(om1, jx[s], om * (rho[s] * vx));
-                const DF o = df_sub(df_sum3(f[s][1], f[s][5], f[s][8]), df_sum3(f[s][3], f[s][7], f[s][6]));
-                const float half = 0.5f * ((t - o.hi) - o.lo);
-                f[s][1] += half;
-                f[s][3] -= half;
-            }
-            // y: pair 2 / 4
-            {
-                const float t = fmaf(om1, jy[s], om * (rho[s] * vy));
-                const DF o = df_sub(df_sum3(f[s][2], f[s][5], f[s][6]), df_sum3(f[s][4], f[s][7], f[s][8]));
-                const float half = 0.5f * ((t - o.hi) - o.lo);
-                f[s][2] += half;
-                f[s][4] -= half;
-            }
-            DF m = {f[s][1], 0.0f};    // axis directions (weight 1/9) before the diagonals
-#pragma unroll
-            for (int i = 2; i < 9; ++i) df_fast_add(m, f[s][i]);
-            f[s][0] = (rr[s].hi - m.hi) + (rr[s].lo - m.lo);
+            for (int i = 0; i < 9; ++i) f[s][i] = fmaf(om, feq[i] - f[s][i], f[s][i]);
+            continue;
         }
+        float in[5], d[9];
+#pragma unroll
+        for (int i = 1; i < 5; ++i) in[i] = f[s][i];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float o = fmaf(om, feq[i] - f[s][i], f[s][i]);
+            d[i] = o - f[s][i];
+            f[s][i] = o;
+        }
+        const float Jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
+        const float Jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+        const float hx = 0.5f * (om * fmaf(rho[s], vx, -jx[s]) - Jx);
+        const float hy = 0.5f * (om * fmaf(rho[s], vy, -jy[s]) - Jy);
+        f[s][1] += hx;
+        f[s][3] -= hx;
+        f[s][2] += hy;
+        f[s][4] -= hy;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) d[i] = f[s][i] - in[i];
+        const float m = ((d[1] + d[2]) + (d[3] + d[4])) + ((d[5] + d[6]) + (d[7] + d[8]));
+        f[s][0] -= m;
     }
 }
 

@@ -361,7 +361,7 @@ extern "C" lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* t
         h->p.tile_y = best_ty;
         destroy_graphs(h);
     } else {
-        const int cand[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128};
+        const int cand[] = {0, 8, 12, 16, 24, 32, 48, 64, 96, 128};   // 0: the kernel's own default
         cudaEvent_t a, b;
         LBM_TRY(cudaEventCreate(&a), "event");
         LBM_TRY(cudaEventCreate(&b), "event");

@@ -8,6 +8,8 @@
 //     S_i(x, y) = B_i(x - c_ix, y - c_iy)   if 0 <= y - c_iy < ny
 //     S_i(x, y) = B_opp(i)(x, y)            otherwise (bounce-back at the wall)
 // Layout: structure of arrays [component][direction][y][pitch], x fastest.
+#include <algorithm>
+
 #include "collide.cuh"
 
 namespace lbm {
@@ -560,23 +562,29 @@ step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
 }
 
 // ---------------------------------------------------------------------------
-// Block-staged fused pull stream-collide.  A block of 128 threads owns 126
-// columns [x0, x0 + 126) and tile_y rows; thread t handles column x0 - 1 + t, so
-// the two edge threads only supply the halo densities of their neighbours.  Input
-// rows are brought into shared memory by bulk asynchronous copies (cp.async.bulk,
-// one mbarrier per stage) issued by one thread: row r of all 18 planes, a 16-byte
-// aligned window of kBlockWin columns covering [x0 - 3, x0 + 129), lands in stage
-// (r - rfirst) mod kBlockStages.  All pulls read shared memory; each input value
-// crosses HBM once per tile and two rows ahead of the sweep are in flight.  The
-// densities of three rows are exchanged through a shared-memory ring (one block
-// barrier per row).
+// Block-staged fused pull stream-collide.  A block of 128 threads owns 128 columns
+// [x0, x0 + 128) and the rows [y0, y1) of one of gridDim.y tiles (the ny rows are
+// split evenly over the tiles); thread t handles column x0 + t, and threads 64 and
+// 65 also supply the densities of the halo columns x0 - 1 and x0 + 128.  Input rows
+// are brought into shared memory by bulk asynchronous copies (cp.async.bulk, one
+// mbarrier per stage), one plane per lane of lanes 0-17 of warp 0: row r of all 18
+// planes, a 16-byte aligned window of BlockWin<T> columns covering [x0 - 2, x0 + 130),
+// lands in stage (r - rfirst) mod kBlockStages.  All pulls read shared memory; each
+// input value crosses HBM once per tile and two rows ahead of the sweep are in
+// flight.  The densities of three rows are exchanged through a shared-memory ring
+// (one block barrier per row).
 // ---------------------------------------------------------------------------
 constexpr int kBlockStages = 5;   // rows y..y+2 in use + 2 rows prefetched (4 stages / 5 blocks per SM measured slower)
-constexpr int kOwned = kThreadsX - 2;
-constexpr int kBlockWin = 144;   // >= 128 + 2 + 7 (alignment slack), 16-byte multiple for 2- and 4-byte types
+template <typename T> struct BlockWin {
+    // 132 columns plus the alignment slack of the window start, in 16-byte units
+    static constexpr int kAlign = 16 / (int)sizeof(T);
+    static constexpr int value = (132 + kAlign - 1 + kAlign - 1) / kAlign * kAlign;
+};
 
 template <typename T>
-size_t block_smem_bytes() { return (size_t)kBlockStages * 18 * kBlockWin * sizeof(T) + kBlockStages * sizeof(uint64_t); }
+size_t block_smem_bytes() {
+    return (size_t)kBlockStages * 18 * BlockWin<T>::value * sizeof(T) + kBlockStages * sizeof(uint64_t);
+}
 
 // Post-streaming populations of window column k on row yo from the stages holding
 // rows yo-1 (S), yo (C), yo+1 (N) (bounce-back on the wall rows).
@@ -584,6 +592,7 @@ template <typename T>
 __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* __restrict__ stC,
                                            const T* __restrict__ stN, bool bottom, bool top, int k,
                                            const float shift[2], float f[2][9]) {
+    constexpr int W = BlockWin<T>::value;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
@@ -591,11 +600,11 @@ __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* _
             const int pl = s * 9 + i;
             T v;
             if (cy(i) == 0) {
-                v = stC[pl * kBlockWin + k - cx(i)];
+                v = stC[pl * W + k - cx(i)];
             } else if (cy(i) == 1) {
-                v = bottom ? stC[(s * 9 + opp(i)) * kBlockWin + k] : stS[pl * kBlockWin + k - cx(i)];
+                v = bottom ? stC[(s * 9 + opp(i)) * W + k] : stS[pl * W + k - cx(i)];
             } else {
-                v = top ? stC[(s * 9 + opp(i)) * kBlockWin + k] : stN[pl * kBlockWin + k - cx(i)];
+                v = top ? stC[(s * 9 + opp(i)) * W + k] : stN[pl * W + k - cx(i)];
             }
             float fv = to_f<T>(v);
             if (IsShifted<T>::value) fv += wf(i) * shift[s];
@@ -606,43 +615,49 @@ __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* _
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsX, 4)
-step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
+    constexpr int W = BlockWin<T>::value;
+    constexpr int kAlign = BlockWin<T>::kAlign;
     extern __shared__ __align__(128) unsigned char dsm[];
     T* stage = reinterpret_cast<T*>(dsm);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kBlockStages * 18 * kBlockWin * sizeof(T));
-    __shared__ float sR[4][2][kThreadsX];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kBlockStages * 18 * W * sizeof(T));
+    __shared__ float sR[4][2][kThreadsX + 2];   // slot 1 + t: column x0 + t; 0 and 129: halo columns
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * kOwned;
-    const int y0 = blockIdx.y * tile_y;
-    const int y1 = min(y0 + tile_y, g.ny);
+    const int x0 = blockIdx.x * kThreadsX;
+    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
+    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
     const int rfirst = max(y0 - 2, 0);
     const int rlast = min(y1 + 1, g.ny - 1);
-    const int x = x0 - 1 + t;
-    const bool owner = t >= 1 && t <= kOwned && x < g.nx;
-    constexpr int kAlign = 16 / (int)sizeof(T);
-    const int e0 = g.origin + x0 - 3;
+    const int x = x0 + t;
+    const bool owner = x < g.nx;
+    const bool dens = x <= g.nx;   // column nx is the periodic ghost of column 0
+    const int e0 = g.origin + x0 - 2;
     const int slack = e0 % kAlign;
     const int k = t + 2 + slack;
+    // threads 64 / 65: the halo columns x0 - 1 / x0 + 128 (window columns 1 / 130 + slack)
+    const bool halo = t == 64 || t == 65;
+    const int kh = t == 64 ? 1 + slack : 130 + slack;
+    const int sh = t == 64 ? 0 : kThreadsX + 1;
     const T* win = fin + (e0 - slack);
     const float shift[2] = {ph.shift[0], ph.shift[1]};
-    const uint32_t row_bytes = kBlockWin * sizeof(T);
+    const uint32_t row_bytes = W * sizeof(T);
 
     if (t == 0) {
         for (int j = 0; j < kBlockStages; ++j) mbar_init(&bar[j], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    int next = rfirst;  // next row to issue (thread 0)
-    auto issue = [&](int r) {
+    int next = rfirst;  // next row to issue (every lane of warp 0 keeps the same count)
+    auto issue = [&](int r) {   // warp 0, all lanes
         const int j = (r - rfirst) % kBlockStages;
         uint64_t* b = &bar[j];
-        mbar_expect_tx(b, 18 * row_bytes);
-        T* dst = stage + (size_t)j * 18 * kBlockWin;
-        const T* src = win + (size_t)r * g.pitch;
-#pragma unroll 1
-        for (int p = 0; p < 18; ++p) bulk_copy_g2s(dst + p * kBlockWin, src + (size_t)p * g.plane, row_bytes, b);
+        if (t == 0) mbar_expect_tx(b, 18 * row_bytes);
+        __syncwarp();
+        if (t < 18)
+            bulk_copy_g2s(stage + (size_t)j * 18 * W + t * W, win + (size_t)r * g.pitch + (size_t)t * g.plane,
+                          row_bytes, b);
     };
-    if (t == 0)
+    if (t < 32)
         for (; next <= rlast && next < rfirst + kBlockStages; ++next) issue(next);
     auto wait_row = [&](int r) {
         if (r >= rfirst && r <= rlast)
@@ -650,65 +665,73 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
     };
     auto stage_of = [&](int r) -> const T* {
         const int rr = min(max(r, rfirst), rlast);
-        return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * kBlockWin;
+        return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * W;
     };
-    auto pull_row = [&](int yo, float f[2][9]) {
+    auto pull_row = [&](int yo, int kk, float f[2][9]) {
         if (yo > 0 && yo < g.ny - 1)   // interior row (uniform over the block): no bounce-back selects
-            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, k, shift, f);
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, kk, shift, f);
         else
-            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, k, shift, f);
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, kk, shift, f);
+    };
+    // densities of row yo into ring slot yo & 3 (zero for columns past nx)
+    auto densities = [&](int yo, float f[2][9]) {
+        pull_row(yo, k, f);
+        const int sl = yo & 3;
+        sR[sl][0][t + 1] = dens ? sum9(f[0]) : 0.0f;
+        sR[sl][1][t + 1] = dens ? sum9(f[1]) : 0.0f;
+        if (halo) {
+            float fh[2][9];
+            pull_row(yo, kh, fh);
+            sR[sl][0][sh] = sum9(fh[0]);
+            sR[sl][1][sh] = sum9(fh[1]);
+        }
     };
 
     float fa[2][9], fb[2][9];
-    {   // density of row y0 - 1 (zero on the virtual wall row)
-        const int slot = (y0 - 1) & 3;
-        float rA = 0.0f, rB = 0.0f;
-        if (y0 > 0) {
-            wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
-            pull_row(y0 - 1, fb);
-            rA = sum9(fb[0]); rB = sum9(fb[1]);
-        }
-        sR[slot][0][t] = rA; sR[slot][1][t] = rB;
+    if (y0 > 0) {   // densities of row y0 - 1 (zero on the virtual wall row)
+        wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
+        densities(y0 - 1, fb);
+    } else {
+        const int sl = (y0 - 1) & 3;
+        sR[sl][0][t + 1] = 0.0f; sR[sl][1][t + 1] = 0.0f;
+        if (halo) { sR[sl][0][sh] = 0.0f; sR[sl][1][sh] = 0.0f; }
     }
     wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
-    pull_row(y0, fa);
-    sR[y0 & 3][0][t] = sum9(fa[0]);
-    sR[y0 & 3][1][t] = sum9(fa[1]);
-    // everybody is past the prologue's reads of row y0 - 2: its stage can take row y0 + 2
+    densities(y0, fa);
+    // everybody is past the prologue's reads of row y0 - 2: its stage can take row y0 + 3
     __syncthreads();
-    if (t == 0) {
+    if (t < 32) {
         fence_proxy_async_smem();
         for (; next <= rlast && next - kBlockStages <= y0 - 2; ++next) issue(next);
     }
 
     auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
-        const int sn = (y + 1) & 3;
         if (y + 1 < g.ny) {
             wait_row(y + 2);
-            pull_row(y + 1, nxt);
-            sR[sn][0][t] = sum9(nxt[0]);
-            sR[sn][1][t] = sum9(nxt[1]);
+            densities(y + 1, nxt);
         } else {
-            sR[sn][0][t] = 0.0f;
-            sR[sn][1][t] = 0.0f;
+            const int sl = (y + 1) & 3;
+            sR[sl][0][t + 1] = 0.0f; sR[sl][1][t + 1] = 0.0f;
+            if (halo) { sR[sl][0][sh] = 0.0f; sR[sl][1][sh] = 0.0f; }
         }
         __syncthreads();
         // every thread is past its reads of rows < y: refill those stages
-        if (t == 0) {
+        if (t < 32) {
             fence_proxy_async_smem();
             for (; next <= rlast && next - kBlockStages <= y - 1; ++next) issue(next);
         }
         if (owner) {
-            const int s0 = (y - 1) & 3, s1 = y & 3, s2 = sn;
+            const int s0 = (y - 1) & 3, s1 = y & 3, s2 = (y + 1) & 3;
+            const int c = t + 1;
             Nbr pA, pB;
-            pA.E = sR[s1][0][t + 1]; pA.W = sR[s1][0][t - 1];
-            pA.N = sR[s2][0][t];     pA.S = sR[s0][0][t];
-            pA.NE = sR[s2][0][t + 1]; pA.NW = sR[s2][0][t - 1];
-            pA.SE = sR[s0][0][t + 1]; pA.SW = sR[s0][0][t - 1];
-            pB.E = sR[s1][1][t + 1]; pB.W = sR[s1][1][t - 1];
-            pB.N = sR[s2][1][t];     pB.S = sR[s0][1][t];
-            pB.NE = sR[s2][1][t + 1]; pB.NW = sR[s2][1][t - 1];
-            pB.SE = sR[s0][1][t + 1]; pB.SW = sR[s0][1][t - 1];
+            pA.E = sR[s1][0][c + 1]; pA.W = sR[s1][0][c - 1];
+            pA.N = sR[s2][0][c];     pA.S = sR[s0][0][c];
+            pA.NE = sR[s2][0][c + 1]; pA.NW = sR[s2][0][c - 1];
+            pA.SE = sR[s0][0][c + 1]; pA.SW = sR[s0][0][c - 1];
+            pB.E = sR[s1][1][c + 1]; pB.W = sR[s1][1][c - 1];
+            pB.N = sR[s2][1][c];     pB.S = sR[s0][1][c];
+            pB.NE = sR[s2][1][c + 1]; pB.NW = sR[s2][1][c - 1];
+            pB.SE = sR[s0][1][c + 1]; pB.SW = sR[s0][1][c - 1];
             collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
             store_site<T>(fout, g, y, x, cur, shift);
         }
@@ -843,6 +866,17 @@ __global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, fl
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Row tiles of the block-staged kernel: tile_y > 0 asks for at most tile_y rows per
+// tile; 0 fills the device's resident block slots exactly once (one wave, every SM
+// equally loaded) unless that leaves fewer than kMinTileRows rows per tile.
+int block_tiles_y(int ny, int tiles_x, int tile_y, int slots) {
+    constexpr int kMinTileRows = 16;
+    if (tile_y > 0) return (ny + tile_y - 1) / tile_y;
+    const int per_wave = std::max(1, slots / tiles_x);
+    const int fit = std::max(1, ny / kMinTileRows);
+    return std::min(per_wave, fit);
+}
+
 template <typename T>
 static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t st) {
     const Grid& g = L.grid;
@@ -853,17 +887,23 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         density_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, g, L.phys);
         collide_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, (T*)L.fout, g, L.phys, L.flag);
     } else if (kernel == LBM_KERNEL_STAGED) {
-        const int ty = L.tile_y > 0 ? L.tile_y : 32;
         const size_t smem = block_smem_bytes<T>();
-        static bool attr_set = false;   // one per instantiation
-        if (!attr_set) {
+        static int tiles_auto = 0;   // one per instantiation: resident blocks on the device
+        if (tiles_auto == 0) {
             cudaError_t e = cudaFuncSetAttribute(step_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
-            attr_set = true;
+            int dev = 0, sms = 0, occ = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_block_kernel<T>, kThreadsX, smem)) !=
+                cudaSuccess)
+                return e;
+            tiles_auto = std::max(1, sms * occ);
         }
-        dim3 grid((g.nx + kOwned - 1) / kOwned, (g.ny + ty - 1) / ty);
-        step_block_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, ty, L.flag);
+        const int gx = (g.nx + kThreadsX - 1) / kThreadsX;
+        dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, tiles_auto));
+        step_block_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, L.flag);
     } else if (kernel == LBM_KERNEL_PIPE) {
         const int ty = L.tile_y > 0 ? L.tile_y : 32;
         const size_t smem = pipe_smem_bytes<T>();
