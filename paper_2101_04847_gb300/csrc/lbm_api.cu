@@ -293,10 +293,11 @@ cudaError_t handle_restore_state(lbm_handle* h) {
 cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy) {
     cudaError_t e = launch_fields(diag_launch(h), nullptr, h->stream);
     const size_t n = (size_t)h->p.nx * h->p.ny;
-    *rA = h->scratch();
-    *rB = h->scratch() + n;
-    *ux = h->scratch() + 4 * n;
-    *uy = h->scratch() + 5 * n;
+    const double* F = h->scratch() + diag_fields_offset(h->p.nx, h->p.ny);
+    *rA = F;
+    *rB = F + n;
+    *ux = F + 2 * n;
+    *uy = F + 3 * n;
     return e;
 }
 cudaError_t handle_pull_S(lbm_handle* h, double* S) {
@@ -653,11 +654,12 @@ lbm_status lbm_get_fields(lbm_handle* h, double* rhoA, double* rhoB, double* ux,
     lbm::DiagLaunch D = diag_launch(h);
     LBM_TRY(lbm::launch_fields(D, nullptr, h->stream), "fields kernels");
     const size_t n = (size_t)h->p.nx * h->p.ny;
-    double* sc = h->scratch();
+    const double* F = h->scratch() + lbm::diag_fields_offset(h->p.nx, h->p.ny);
     double* dst[4] = {rhoA, rhoB, ux, uy};
-    const size_t off[4] = {0, n, 4 * n, 5 * n};   // M[0], M[1], U[0], U[1]
     for (int k = 0; k < 4; ++k)
-        if (dst[k]) LBM_TRY(cudaMemcpyAsync(dst[k], sc + off[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy fields");
+        if (dst[k])
+            LBM_TRY(cudaMemcpyAsync(dst[k], F + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                    "copy fields");
     LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
     return LBM_OK;
 }

@@ -136,9 +136,12 @@ struct DiagLaunch {
 };
 size_t diag_scratch_doubles(int nx, int ny);
 size_t diag_partials_doubles(int nx, int ny);
+// offset (in doubles) of the rho_A, rho_B, ux, uy fields (double [ny][nx] each) that
+// launch_fields leaves in the scratch region
+size_t diag_fields_offset(int nx, int ny);
 cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st);
-// rho_A, rho_B, ux, uy (double [ny][nx] each) into `fields` (4 * nx * ny doubles);
-// uses scratch (15 doubles per site)
+// rho_A, rho_B, ux, uy (double [ny][nx] each) into the scratch region at
+// diag_fields_offset (uses the whole scratch: 15 doubles per site)
 cudaError_t launch_fields(const DiagLaunch& D, double* fields, cudaStream_t st);
 
 }  // namespace lbm
