@@ -9,7 +9,8 @@ advances both components).  Population buffers (2 x 151 MB) exceed the 129 MB
 L2, so no separate L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--storage f32|f16|bf16] [--kernel fused|two_pass] [--tile-y T]
+                  [--storage f32|f16|bf16] [--kernel staged|warp|pipe|fused|two_pass]
+                  [--tile-y T] [--nx NX --ny NY] [--ensemble M] [--storage-study STEPS]
 
 --impl reference times the FP64 CPU oracle on the host on a bounded sample of
 the same workload.  With torchrun (N > 1) every rank advances its own
@@ -61,10 +62,14 @@ def dist_env():
     return ws, rank, local
 
 
+STEP_SOURCES = ("step_kernels.cu", "collide.cuh", "lattice.cuh", "lbm_internal.cuh")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the step kernels are compiled from."""
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_2101_04847_gb300" / "csrc").glob("*")):
-        h.update(p.read_bytes())
+    for name in STEP_SOURCES:
+        h.update((ROOT / "paper_2101_04847_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -362,6 +367,62 @@ def run_ensemble(args):
     print(json.dumps(out), flush=True)
 
 
+def run_storage_study(args):
+    """The same realisation advanced with FP32, FP16 and BF16 population storage; the
+    16-bit runs' diagnostics are compared with the FP32 run's at checkpoints (the FP32
+    path matches the FP64 oracle to ~3e-6 on the small grid, and the oracle is out of
+    reach at this size).  Each storage's rate and roofline fraction are timed too."""
+    import torch
+
+    from paper_2101_04847_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    params = workload(args)
+    params["seed"] = 1
+    total = args.storage_study
+    nchk = 5
+    chunk = max(1, total // nchk)
+    budget = ("flux_pb", "flux_K", "flux_tau", "viscous", "buoyancy")
+    keys = ("E_k", "E_p", "h", "L_int", "viscous", "enstrophy", "mass_A", "mass_B") + budget
+    series, rates = {}, {}
+    stream = torch.cuda.Stream()
+    for storage in ("f32", "f16", "bf16"):
+        with torch.cuda.stream(stream):
+            s = lbm.Solver(storage=storage, kernel=args.kernel, tile_y=args.tile_y, **params)
+        s.step(LB_STEPS_PER_STEP)   # warm-up of the graphs
+        s.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        rows = []
+        for _ in range(nchk):
+            a.record(stream)
+            s.step(chunk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            d = s.diagnostics(check=False)
+            rows.append({k: float(d[k]) for k in keys} | {"status": int(d["status"])})
+        s.close()
+        series[storage] = rows
+        mlups = args.nx * args.ny * chunk * nchk / (ms * 1e-3) / 1e6
+        rates[storage] = {"MLUPS": round(mlups, 1), "launch_ms": round(ms / (chunk * nchk), 5),
+                          "roofline_frac": round(BYTES_PER_SITE[storage] * mlups * 1e6 / 1e9 / measured_peak_hbm()[0], 4)}
+    errors = {}
+    for storage in ("f16", "bf16"):
+        per = []
+        for ref, got in zip(series["f32"], series[storage]):
+            scale = max(abs(ref[k]) for k in budget)
+            per.append({k: round(abs(got[k] - ref[k]) / (scale if k in budget else max(abs(ref[k]), 1e-300)), 6)
+                        for k in keys})
+        errors[storage] = per
+    out = {"kind": "storage_study", "workload": config_of(args, 1)["workload"], "steps": chunk * nchk,
+           "checkpoints": [chunk * (i + 1) for i in range(nchk)], "rates": rates,
+           "relative_error_vs_f32": errors,
+           "f32_series": series["f32"],
+           "note": "budget terms relative to the largest budget term at that checkpoint"}
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(args, budget_s: float) -> dict:
     """The FP64 numpy oracle as it stands, on the host, one LB step at a time on the full
     grid until about `budget_s` seconds of CPU work are done."""
@@ -424,6 +485,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
+    ap.add_argument("--storage-study", dest="storage_study", type=int, default=0,
+                    help="advance FP32, FP16 and BF16 storage this many LB steps and compare their diagnostics")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -431,6 +494,8 @@ def main():
         run_reference(args)
     elif args.ensemble:
         run_ensemble(args)
+    elif args.storage_study:
+        run_storage_study(args)
     else:
         run_ours(args)
 
