@@ -309,6 +309,9 @@ def run_ensemble(args):
 
     torch.cuda.set_device(0)
     members = ensemble_members(args.ensemble)
+    if args.ensemble_grid:   # every member on one grid (e.g. small grids that cannot fill the GPU alone)
+        nx, ny = (int(v) for v in args.ensemble_grid.lower().split("x"))
+        members = [dict(m, nx=nx, ny=ny) for m in members]
     lb_steps = 20
     params = [lbm.default_params(kernel="staged", **m) for m in members]
     stream = torch.cuda.Stream()
@@ -334,7 +337,7 @@ def run_ensemble(args):
     seq_ms = 0.0
     for m in members:
         with torch.cuda.stream(stream):
-            s = lbm.Solver(lbm.default_params(kernel="staged", tile_y=tile_y, **m))
+            s = lbm.Solver(lbm.default_params(kernel="staged", **m))   # each run with its own default tiling
         for _ in range(args.warmup):
             s.step(lb_steps)
         torch.cuda.synchronize()
@@ -353,8 +356,10 @@ def run_ensemble(args):
         "metric": METRIC, "value": round(agg, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ens_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16", "data": "synthetic",
-        "config": {"workload": f"ensemble of {len(members)} realisations, grids from 512x1024/1024x2048/2048x4096, "
-                               f"G from 0/1.2/1.4, FP32 or FP16 storage, one launch per LB step",
+        "config": {"workload": f"ensemble of {len(members)} realisations, grids "
+                               + (f"all {args.ensemble_grid}" if args.ensemble_grid
+                                  else "from 512x1024/1024x2048/2048x4096")
+                               + ", G from 0/1.2/1.4, FP32 or FP16 storage, one launch per LB step",
                    "members": [f"{m['nx']}x{m['ny']} G={m['G']} {m['storage']}" for m in members],
                    "lb_steps_per_step": lb_steps, "tile_y": tile_y},
         "sequential": {"value": round(seq, 1), "unit": "MLUPS", "speedup": round(agg / seq, 3)},
@@ -485,6 +490,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
+    ap.add_argument("--ensemble-grid", dest="ensemble_grid", default="",
+                    help="with --ensemble: put every member on this NXxNY grid instead of the drawn ones")
     ap.add_argument("--storage-study", dest="storage_study", type=int, default=0,
                     help="advance FP32, FP16 and BF16 storage this many LB steps and compare their diagnostics")
     args = ap.parse_args()

@@ -205,8 +205,8 @@ lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* tile_y, doub
  * storage; each uses the staged kernel and its own workspace. ---- */
 typedef struct lbm_ensemble lbm_ensemble;
 
-/* n parameter sets (1..256); tile_y of members[0] (or the default) is used for
- * all.  cuda_stream: a cudaStream_t shared by all members, or NULL for one owned
+/* n parameter sets (1..256); tile_y of members[0] is the rows per tile of every
+ * member (0: chosen so that the tiles fill the device's block slots in whole waves).  cuda_stream: a cudaStream_t shared by all members, or NULL for one owned
  * by the ensemble. */
 lbm_status lbm_ens_create(int32_t n, const lbm_params* members, void* cuda_stream, lbm_ensemble** out);
 
@@ -223,7 +223,8 @@ lbm_status lbm_ens_member(lbm_ensemble* e, int32_t i, lbm_handle** out);
 /* Diagnostics of every member into out[0..n-1]; synchronises. */
 lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out);
 
-/* Pick tile_y for the whole ensemble by timing candidates; states are kept. */
+/* Pick tile_y for the whole ensemble by timing candidates (0, the slot-filling
+ * default, among them); states are kept.  tile_y receives the rows per tile in use. */
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y, double* ms_per_step);
 
 void lbm_ens_destroy(lbm_ensemble* e);

@@ -1,7 +1,7 @@
 // Ensembles of independent realisations (the paper runs at least 10 per
 // experiment, Section 2): one kernel launch per time step advances every member
-// (ensemble_step_kernel, step_kernels.cu), and chunks of steps are captured in
-// CUDA graphs.  Members may differ in grid size, physics and storage type; each
+// (ensemble_step_kernel, step_kernels.cu: the block-staged tile code over a flat
+// list of every member's tiles), and chunks of steps are captured in CUDA graphs.  Members may differ in grid size, physics and storage type; each
 // member is a full lbm_handle (init, diagnostics, fields, checkpoints) that only
 // the ensemble steps.
 #include "lbm_internal.cuh"
@@ -33,7 +33,9 @@ struct lbm_ensemble {
     std::vector<lbm::EnsMember> table;
     lbm::EnsMember* d_table = nullptr;
     int total_tiles = 0;
-    int tile_y = 0;
+    int tile_y = 0;       // requested rows per tile; 0: chosen from the device's block slots
+    int rows = 0;         // rows per tile in use
+    size_t smem = 0;      // dynamic shared memory per block (largest storage type present)
     int parity = 0;
     int64_t step = 0;
     cudaStream_t stream = nullptr;
@@ -50,11 +52,57 @@ void ens_drop_graphs(lbm_ensemble* e) {
     }
 }
 
+int tiles_of(const lbm::Grid& g, int rows, int* tx, int* ty) {
+    *tx = (g.nx + 127) / 128;
+    *ty = std::min(g.ny, std::max(1, (g.ny + rows - 1) / rows));
+    return *tx * *ty;
+}
+
+// Rows per tile when none is requested: the height whose tile count fills the
+// resident block slots in whole waves best, weighted by the share of rows that
+// are not halo (3 halo rows per tile).
+int auto_rows(const lbm_ensemble* e, int slots) {
+    int best = 32;
+    double best_score = -1.0;
+    for (int rows = 12; rows <= 256; ++rows) {
+        long long tiles = 0;
+        for (lbm_handle* h : e->members) {
+            int tx, ty;
+            tiles += tiles_of(lbm::handle_grid(h), rows, &tx, &ty);
+        }
+        const long long waves = (tiles + slots - 1) / slots;
+        const double score = (double)tiles / (double)(waves * slots) * rows / (rows + 3.0);
+        if (score > best_score + 1e-9) {
+            best_score = score;
+            best = rows;
+        }
+    }
+    return best;
+}
+
 // (Re)build the member table for the current tile height and upload it.
 lbm_status ens_build_table(lbm_ensemble* e) {
     e->table.clear();
+    e->smem = 0;
+    for (lbm_handle* h : e->members)
+        e->smem = std::max(e->smem, lbm::block_tile_smem_bytes(lbm::handle_params(h).storage));
+    if (e->tile_y > 0) {
+        e->rows = e->tile_y;
+    } else {
+        cudaError_t err = cudaSuccess;
+        const int slots = lbm::ensemble_slots(e->smem, &err);
+        ENS_TRY(err, "ensemble occupancy");
+        e->rows = auto_rows(e, slots);
+    }
+    // Tiles of one storage type are contiguous in the flat list, so that the blocks
+    // resident at one time mostly run one instantiation of the tile code (mixing
+    // them on an SM thrashes its instruction cache).
+    std::vector<lbm_handle*> order;
+    for (int st : {LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16})
+        for (lbm_handle* h : e->members)
+            if (lbm::handle_params(h).storage == st) order.push_back(h);
     int begin = 0;
-    for (lbm_handle* h : e->members) {
+    for (lbm_handle* h : order) {
         lbm::EnsMember m;
         m.grid = lbm::handle_grid(h);
         m.phys = lbm::handle_phys(h);
@@ -62,8 +110,7 @@ lbm_status ens_build_table(lbm_ensemble* e) {
         m.buf[1] = lbm::handle_buffer(h, 1);
         m.flag = lbm::handle_flag(h);
         m.storage = lbm::handle_params(h).storage;
-        m.tile_y = e->tile_y;
-        const int tiles = lbm::warp_tiles(m.grid, m.tile_y, &m.tiles_x);
+        const int tiles = tiles_of(m.grid, e->rows, &m.tiles_x, &m.tiles_y);
         m.tile_begin = begin;
         begin += tiles;
         e->table.push_back(m);
@@ -78,7 +125,8 @@ lbm_status ens_build_table(lbm_ensemble* e) {
 
 lbm_status ens_launch(lbm_ensemble* e, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
-        ENS_TRY(lbm::launch_ensemble_step(e->d_table, (int)e->members.size(), e->total_tiles, e->parity, e->stream),
+        ENS_TRY(lbm::launch_ensemble_step(e->d_table, (int)e->members.size(), e->total_tiles, e->parity, e->smem,
+                                          e->stream),
                 "ensemble step");
         e->parity ^= 1;
     }
@@ -92,7 +140,7 @@ lbm_status ens_graph(lbm_ensemble* e, cudaGraphExec_t* out) {
         ENS_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         for (int k = 0; k < kEnsGraphChunk; ++k) {
             cudaError_t err = lbm::launch_ensemble_step(e->d_table, (int)e->members.size(), e->total_tiles,
-                                                        (par + k) & 1, e->stream);
+                                                        (par + k) & 1, e->smem, e->stream);
             if (err != cudaSuccess) {
                 cudaStreamEndCapture(e->stream, &g);
                 if (g) cudaGraphDestroy(g);
@@ -140,10 +188,10 @@ lbm_status lbm_ens_create(int32_t n, const lbm_params* params, void* cuda_stream
         }
         e->own_stream = true;
     }
-    e->tile_y = params[0].tile_y > 0 ? params[0].tile_y : lbm::default_tile_y();
+    e->tile_y = params[0].tile_y > 0 ? params[0].tile_y : 0;
     for (int i = 0; i < n; ++i) {
         lbm_params p = params[i];
-        p.kernel = LBM_KERNEL_WARP;
+        p.kernel = LBM_KERNEL_STAGED;
         lbm_handle* h = nullptr;
         lbm_status st = lbm_create_ex(&p, nullptr, 0, e->stream, &h);
         if (st != LBM_OK) {
@@ -218,7 +266,7 @@ lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out) {
 
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y_out, double* ms_out) {
     if (!e) return ens_fail(LBM_EINVAL, "ensemble is NULL");
-    const int cand[] = {8, 16, 24, 32, 48, 64, 96};
+    const int cand[] = {0, 12, 16, 20, 24, 32, 48, 64, 96};   // 0: the slot-filling default
     cudaEvent_t a, b;
     ENS_TRY(cudaEventCreate(&a), "event");
     ENS_TRY(cudaEventCreate(&b), "event");
@@ -256,7 +304,7 @@ lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y_out, double* ms_out) {
     e->tile_y = best_ty;
     lbm_status st = ens_build_table(e);
     if (st != LBM_OK) return st;
-    if (tile_y_out) *tile_y_out = best_ty;
+    if (tile_y_out) *tile_y_out = e->rows;
     if (ms_out) *ms_out = best_ms;
     return LBM_OK;
 }

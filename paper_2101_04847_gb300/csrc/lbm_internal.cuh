@@ -75,15 +75,20 @@ struct EnsMember {
     void* buf[2];        // the two population buffers (input = buf[parity])
     int* flag;           // the member's guard flag
     int storage;         // lbm_storage
-    int tile_y;          // rows per warp tile
-    int tiles_x;         // warp tiles along x
+    int tiles_x;         // block tiles along x (128 columns each)
+    int tiles_y;         // block tiles along y (rows split evenly)
     int tile_begin;      // index of the member's first tile in the flat list
 };
 
 // ensemble / tiling helpers (step_kernels.cu)
 int warp_tiles(const Grid& g, int tile_y, int* tiles_x);
 int default_tile_y();
-cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, cudaStream_t st);
+// dynamic shared memory of one block tile for a storage type
+size_t block_tile_smem_bytes(int storage);
+// resident blocks of the ensemble kernel on the current device with `smem` bytes each
+int ensemble_slots(size_t smem, cudaError_t* err);
+cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, size_t smem,
+                                 cudaStream_t st);
 
 // handle accessors for the ensemble (lbm_api.cu)
 void* handle_buffer(lbm_handle* h, int k);

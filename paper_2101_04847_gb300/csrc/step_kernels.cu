@@ -321,39 +321,7 @@ step_warp_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
                  dsm + (size_t)warp * warp_smem_bytes<T>(), flag);
 }
 
-// ---------------------------------------------------------------------------
-// Ensemble step: one launch advances every member by one time step.  Warp w of
-// the launch takes tile w of the flat list that concatenates the members' warp
-// tiles (members may differ in grid, physics and storage type); no member waits
-// for another, so uneven grids need no barrier.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsX, 4)
-ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int total_tiles, int parity) {
-    extern __shared__ __align__(128) unsigned char dsm[];
-    const int warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
-    if (tile >= total_tiles) return;
-    int m = 0;
-    while (m + 1 < n && members[m + 1].tile_begin <= tile) ++m;
-    const EnsMember& M = members[m];
-    const int local = tile - M.tile_begin;
-    const int tx = local % M.tiles_x, ty = local / M.tiles_x;
-    unsigned char* my = dsm + (size_t)warp * warp_smem_bytes<float>();
-    const void* fin = M.buf[parity];
-    void* fout = M.buf[parity ^ 1];
-    switch (M.storage) {
-        case LBM_STORE_F16:
-            warp_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, M.tile_y, tx, ty, my, M.flag);
-            break;
-        case LBM_STORE_BF16:
-            warp_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, M.phys, M.tile_y, tx, ty,
-                                     my, M.flag);
-            break;
-        default:
-            warp_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, M.tile_y, tx, ty, my, M.flag);
-    }
-}
-
+// warp tiles of one grid for the per-warp kernel
 int warp_tiles(const Grid& g, int tile_y, int* tiles_x) {
     const int tx = (g.nx + kWarpOwned - 1) / kWarpOwned;
     if (tiles_x) *tiles_x = tx;
@@ -361,20 +329,6 @@ int warp_tiles(const Grid& g, int tile_y, int* tiles_x) {
 }
 
 int default_tile_y() { return 32; }
-
-cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, cudaStream_t st) {
-    (void)cudaGetLastError();
-    const size_t smem = kWarpsPerBlock * warp_smem_bytes<float>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int blocks = (total_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    ensemble_step_kernel<<<blocks, kThreadsX, smem, st>>>(d_members, n, total_tiles, parity);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Pipelined fused pull stream-collide.  A block of 4 warps shares one ring of
@@ -613,19 +567,21 @@ __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* _
     }
 }
 
+// Density ring of the block tile: slot 1 + t holds column x0 + t, slots 0 and 129
+// the halo columns x0 - 1 and x0 + 128.
+typedef float BlockRing[4][2][kThreadsX + 2];
+
+// One block tile: columns [x0, x0 + 128) and rows [y0, y1) of one grid.  dsm: the
+// block_smem_bytes<T>() of dynamic shared memory (row stages, then the mbarriers).
 template <typename T>
-__global__ void __launch_bounds__(kThreadsX, 4)
-step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
+__device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
+                                           const Physics& ph, int x0, int y0, int y1, unsigned char* dsm,
+                                           BlockRing& sR, int* flag) {
     constexpr int W = BlockWin<T>::value;
     constexpr int kAlign = BlockWin<T>::kAlign;
-    extern __shared__ __align__(128) unsigned char dsm[];
     T* stage = reinterpret_cast<T*>(dsm);
     uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kBlockStages * 18 * W * sizeof(T));
-    __shared__ float sR[4][2][kThreadsX + 2];   // slot 1 + t: column x0 + t; 0 and 129: halo columns
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * kThreadsX;
-    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
-    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
     const int rfirst = max(y0 - 2, 0);
     const int rlast = min(y1 + 1, g.ny - 1);
     const int x = x0 + t;
@@ -740,6 +696,88 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
         row(y, fa, fb);
         if (y + 1 < y1) row(y + 1, fb, fa);
     }
+}
+
+// One grid: block (bx, by) takes columns [128 bx, 128 bx + 128) and the by-th of
+// gridDim.y tiles of (nearly) equal height.
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX, 4)
+step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ BlockRing sR;
+    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
+    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
+    block_tile<T>(fin, fout, g, ph, blockIdx.x * kThreadsX, y0, y1, dsm, sR, flag);
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble step: one launch advances every member by one time step.  Block b takes
+// tile b of the flat list that concatenates the members' block tiles (members in
+// order, each member's tiles row-major) and runs the block-staged tile code with
+// the member's grid, physics and storage type; no member waits for another, so
+// uneven grids need no barrier.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreadsX, 4)
+ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ BlockRing sR;
+    const int tile = blockIdx.x;
+    int lo = 0, hi = n - 1;   // last member whose first tile is <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (members[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    const EnsMember& M = members[lo];
+    const int local = tile - M.tile_begin;
+    const int tx = local % M.tiles_x, ty = local / M.tiles_x;
+    const int y0 = (int)(((long long)ty * M.grid.ny) / M.tiles_y);
+    const int y1 = (int)(((long long)(ty + 1) * M.grid.ny) / M.tiles_y);
+    const void* fin = M.buf[parity];
+    void* fout = M.buf[parity ^ 1];
+    switch (M.storage) {
+        case LBM_STORE_F16:
+            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, tx * kThreadsX, y0, y1, dsm, sR,
+                               M.flag);
+            break;
+        case LBM_STORE_BF16:
+            block_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, M.phys,
+                                      tx * kThreadsX, y0, y1, dsm, sR, M.flag);
+            break;
+        default:
+            block_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, tx * kThreadsX, y0, y1, dsm, sR,
+                              M.flag);
+    }
+}
+
+size_t block_tile_smem_bytes(int storage) {
+    return storage == LBM_STORE_F32 ? block_smem_bytes<float>() : block_smem_bytes<__half>();
+}
+
+// Resident blocks of the ensemble kernel on the current device for `smem` bytes.
+int ensemble_slots(size_t smem, cudaError_t* err) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)block_smem_bytes<float>());
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel, kThreadsX, smem);
+    if (err) *err = e;
+    return std::max(1, sms * occ);
+}
+
+cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, size_t smem,
+                                 cudaStream_t st) {
+    (void)cudaGetLastError();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)block_smem_bytes<float>());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    ensemble_step_kernel<<<total_tiles, kThreadsX, smem, st>>>(d_members, n, parity);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

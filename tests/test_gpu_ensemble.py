@@ -1,9 +1,9 @@
 """Ensemble launch and the tile tuner (GPU).
 
 Every member of an ensemble advanced by the one-launch-per-step kernel must
-match the same realisation advanced alone by the per-warp kernel (the same tile
-code, compiled into another kernel, so equal up to FMA contraction), and tuning
-must leave states untouched.
+match the same realisation advanced alone by the block-staged kernel (the same
+tile code, compiled into another kernel, so equal up to FMA contraction), and
+tuning must leave states untouched.
 """
 import numpy as np
 import pytest
@@ -24,7 +24,7 @@ MEMBERS = [
 def member_params(m, tile_y=0):
     d = inputs.params(inputs.C0, crop_rows=5, g=1e-4)
     d.update(m)
-    return lbm.default_params(kernel="warp", tile_y=tile_y, **d)
+    return lbm.default_params(kernel="staged", tile_y=tile_y, **d)
 
 
 def test_ensemble_members_equal_solo_runs(gpu):
@@ -57,7 +57,7 @@ def test_ensemble_tune_keeps_states(gpu):
         ens.step(10)
         before = [m.populations() for m in ens.members]
         ty, ms = ens.tune()
-        assert ty in (8, 16, 24, 32, 48, 64, 96) and ms > 0
+        assert 12 <= ty <= 256 and ms > 0
         after = [m.populations() for m in ens.members]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)
