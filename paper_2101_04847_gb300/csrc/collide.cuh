@@ -14,6 +14,32 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
     sy = (1.0f / 9.0f) * (r.N - r.S) + (1.0f / 36.0f) * ((r.NE - r.SW) + (r.NW - r.SE));
 }
 
+// Common velocity u = sum_s j_s / tau_s / sum_s rho_s / tau_s (Eq. 1) and the
+// accelerations a_s = F_s / rho_s: Shan-Chen coupling to the other component's
+// pseudopotential, the external (buoyancy, body) accelerations and, on the wall
+// rows, the fluid-boundary force.  Raises bit 0 of the guard flag for a negative
+// or non-finite density.
+__device__ __forceinline__ void velocity_and_accel(const float rho[2], const float jx[2], const float jy[2],
+                                                   const Nbr& psiA, const Nbr& psiB, const Physics& ph, int y,
+                                                   int ny, int* flag, float& ux, float& uy, float ax[2],
+                                                   float ay[2]) {
+    const float rA = rho[0];
+    const float rB = rho[1];
+    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
+    const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
+    ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
+    uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;
+    float nAx, nAy, nBx, nBy;
+    nbr_sum(psiA, nAx, nAy);
+    nbr_sum(psiB, nBx, nBy);
+    ax[0] = -ph.G * nBx + ph.ax_ext;
+    ay[0] = -ph.G * nBy + ph.ay_ext[0];
+    ax[1] = -ph.G * nAx + ph.ax_ext;
+    ay[1] = -ph.G * nAy + ph.ay_ext[1];
+    if (y == 0) { ay[0] += ph.ay_wall_bottom[0]; ay[1] += ph.ay_wall_bottom[1]; }
+    if (y == ny - 1) { ay[0] += ph.ay_wall_top[0]; ay[1] += ph.ay_wall_top[1]; }
+}
+
 // Forced BGK collision of one site (Section 2, Eqs. "Kinetic equation" and
 // "Equilibrium distribution"): f <- f + (f^eq(rho_s, u + tau_s a_s) - f) / tau_s with
 // a_s = F_s / rho_s computed directly (no division by rho_s).  The equilibrium is
@@ -40,22 +66,8 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
         jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
         jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][7]) + (f[s][6] - f[s][8]);
     }
-    const float rA = rho[0];
-    const float rB = rho[1];
-    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
-    const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
-    const float ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
-    const float uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;
-    float nAx, nAy, nBx, nBy;
-    nbr_sum(psiA, nAx, nAy);
-    nbr_sum(psiB, nBx, nBy);
-    float ax[2], ay[2];
-    ax[0] = -ph.G * nBx + ph.ax_ext;
-    ay[0] = -ph.G * nBy + ph.ay_ext[0];
-    ax[1] = -ph.G * nAx + ph.ax_ext;
-    ay[1] = -ph.G * nAy + ph.ay_ext[1];
-    if (y == 0) { ay[0] += ph.ay_wall_bottom[0]; ay[1] += ph.ay_wall_bottom[1]; }
-    if (y == ny - 1) { ay[0] += ph.ay_wall_top[0]; ay[1] += ph.ay_wall_top[1]; }
+    float ux, uy, ax[2], ay[2];
+    velocity_and_accel(rho, jx, jy, psiA, psiB, ph, y, ny, flag, ux, uy, ax, ay);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const float vx = ux + ph.tau[s] * ax[s];
@@ -104,6 +116,48 @@ __device__ __forceinline__ void collide_site(float f[2][9], const Nbr& psiA, con
         for (int i = 1; i < 5; ++i) d[i] = f[s][i] - in[i];
         const float m = ((d[1] + d[2]) + (d[3] + d[4])) + ((d[5] + d[6]) + (d[7] + d[8]));
         f[s][0] -= m;
+    }
+}
+
+// The same collision on shifted populations h_i = f_i - w_i rho0_s (16-bit
+// storage), without forming f: rho_s = rho0_s + sum_i h_i, j_s = sum_i c_i h_i
+// (the shift carries no momentum), and
+//   f^eq_i - w_i rho0_s = w_i (rho_s - rho0_s) + w_i rho_s (9/2 (c_i.u')^2 - 3/2 u'^2 + 3 c_i.u'),
+// so h_i <- h_i + (f^eq_i - w_i rho0_s - h_i) / tau_s.
+__device__ __forceinline__ void collide_shifted(float h[2][9], const Nbr& psiA, const Nbr& psiB,
+                                                const Physics& ph, int y, int ny, int* flag) {
+    float dr[2], rho[2], jx[2], jy[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        dr[s] = sum9(h[s]);
+        rho[s] = ph.shift[s] + dr[s];
+        jx[s] = (h[s][1] - h[s][3]) + (h[s][5] - h[s][7]) + (h[s][8] - h[s][6]);
+        jy[s] = (h[s][2] - h[s][4]) + (h[s][5] - h[s][7]) + (h[s][6] - h[s][8]);
+    }
+    float ux, uy, ax[2], ay[2];
+    velocity_and_accel(rho, jx, jy, psiA, psiB, ph, y, ny, flag, ux, uy, ax, ay);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float vx = ux + ph.tau[s] * ax[s];
+        const float vy = uy + ph.tau[s] * ay[s];
+        const float om = ph.om[s];
+        const float usq = 1.5f * (vx * vx + vy * vy);
+        float feq[9];
+        feq[0] = (4.0f / 9.0f) * fmaf(-rho[s], usq, dr[s]);
+        {   // pairs (1,3), (2,4), (5,7), (6,8)
+            const float c[4] = {vx, vy, vx + vy, vy - vx};
+            const float w[4] = {1.0f / 9.0f, 1.0f / 9.0f, 1.0f / 36.0f, 1.0f / 36.0f};
+            const int a[4] = {1, 2, 5, 6}, b[4] = {3, 4, 7, 8};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float sym = w[q] * fmaf(rho[s], fmaf(4.5f * c[q], c[q], -usq), dr[s]);
+                const float anti = (w[q] * rho[s]) * (3.0f * c[q]);
+                feq[a[q]] = sym + anti;
+                feq[b[q]] = sym - anti;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[s][i] = fmaf(om, feq[i] - h[s][i], h[s][i]);
     }
 }
 

@@ -78,6 +78,63 @@ __device__ __forceinline__ void store_site(T* __restrict__ fout, const Grid& g, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit stores.  Rounding to nearest lets slowly
+// varying populations round the same way step after step, which drifts the
+// masses by several per cent over 10^4 steps.  A value is instead rounded up in
+// magnitude with probability equal to its distance from the lower neighbour, in
+// units of the spacing: uniform random bits are added below the kept mantissa of
+// the FP32 pattern and the sum is truncated.  The random bits are a hash of the
+// site, the component and the unrounded rest population (lowbias32 of C.
+// Wellons' hash prospector), stepped by the PCG multiplier of M. E. O'Neill per
+// value, so a state and its update always round the same way (results are
+// reproducible) while any change of the state changes the rounding.  FP16
+// subnormals (|h| < 2^-14) keep a truncation bias below 2^-24.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t hash_lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+template <typename T> __device__ __forceinline__ T round_stochastic(float v, uint32_t r);
+template <> __device__ __forceinline__ __half round_stochastic<__half>(float v, uint32_t r) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));   // 13 bits dropped
+}
+template <> __device__ __forceinline__ __nv_bfloat16 round_stochastic<__nv_bfloat16>(float v, uint32_t r) {
+    return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r >> 16)));   // 16 bits dropped
+}
+
+// Store the 18 shifted values h of column x on row y (16-bit storage: h is what is
+// stored, no shift applied here), stochastically rounded, plus the periodic ghost
+// copy of the two first / last columns.
+template <typename T>
+__device__ __forceinline__ void store_site_sr(T* __restrict__ fout, const Grid& g, int y, int x,
+                                              const float h[2][9]) {
+    T* q = fout + (size_t)y * g.pitch + g.origin + x;
+    T tv[2][9];
+    const uint32_t site = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        uint32_t r = hash_lowbias32((site * 2u + (uint32_t)s) ^ __float_as_uint(h[s][0]));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            r = r * 747796405u + 2891336453u;
+            tv[s][i] = round_stochastic<T>(h[s][i], r);
+            q[(size_t)(s * 9 + i) * g.plane] = tv[s][i];
+        }
+    }
+    if (x < 2 || x >= g.nx - 2) {
+        T* qg = q + (x < 2 ? g.nx : -g.nx);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) qg[(size_t)(s * 9 + i) * g.plane] = tv[s][i];
+    }
+}
+
 __device__ __forceinline__ float sum9(const float* f) {
     return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
 }

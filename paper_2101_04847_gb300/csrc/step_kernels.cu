@@ -540,12 +540,13 @@ size_t block_smem_bytes() {
     return (size_t)kBlockStages * 18 * BlockWin<T>::value * sizeof(T) + kBlockStages * sizeof(uint64_t);
 }
 
-// Post-streaming populations of window column k on row yo from the stages holding
-// rows yo-1 (S), yo (C), yo+1 (N) (bounce-back on the wall rows).
+// Post-streaming stored values of window column k on row yo from the stages
+// holding rows yo-1 (S), yo (C), yo+1 (N) (bounce-back on the wall rows): the
+// populations for FP32 storage, the shifted values h = f - w rho0 for 16-bit.
 template <typename T>
 __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* __restrict__ stC,
                                            const T* __restrict__ stN, bool bottom, bool top, int k,
-                                           const float shift[2], float f[2][9]) {
+                                           float f[2][9]) {
     constexpr int W = BlockWin<T>::value;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -560,9 +561,7 @@ __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* _
             } else {
                 v = top ? stC[(s * 9 + opp(i)) * W + k] : stN[pl * W + k - cx(i)];
             }
-            float fv = to_f<T>(v);
-            if (IsShifted<T>::value) fv += wf(i) * shift[s];
-            f[s][i] = fv;
+            f[s][i] = to_f<T>(v);
         }
     }
 }
@@ -625,21 +624,26 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     };
     auto pull_row = [&](int yo, int kk, float f[2][9]) {
         if (yo > 0 && yo < g.ny - 1)   // interior row (uniform over the block): no bounce-back selects
-            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, kk, shift, f);
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, kk, f);
         else
-            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, kk, shift, f);
+            pull_block<T>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, kk, f);
     };
-    // densities of row yo into ring slot yo & 3 (zero for columns past nx)
+    // densities of row yo into ring slot yo & 3 (zero for columns past nx); 16-bit
+    // storage holds h = f - w rho0, whose sum is rho - rho0
+    auto density = [&](const float* f, int s) {
+        if constexpr (IsShifted<T>::value) return sum9(f) + shift[s];
+        else return sum9(f);
+    };
     auto densities = [&](int yo, float f[2][9]) {
         pull_row(yo, k, f);
         const int sl = yo & 3;
-        sR[sl][0][t + 1] = dens ? sum9(f[0]) : 0.0f;
-        sR[sl][1][t + 1] = dens ? sum9(f[1]) : 0.0f;
+        sR[sl][0][t + 1] = dens ? density(f[0], 0) : 0.0f;
+        sR[sl][1][t + 1] = dens ? density(f[1], 1) : 0.0f;
         if (halo) {
             float fh[2][9];
             pull_row(yo, kh, fh);
-            sR[sl][0][sh] = sum9(fh[0]);
-            sR[sl][1][sh] = sum9(fh[1]);
+            sR[sl][0][sh] = density(fh[0], 0);
+            sR[sl][1][sh] = density(fh[1], 1);
         }
     };
 
@@ -688,8 +692,13 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
             pB.N = sR[s2][1][c];     pB.S = sR[s0][1][c];
             pB.NE = sR[s2][1][c + 1]; pB.NW = sR[s2][1][c - 1];
             pB.SE = sR[s0][1][c + 1]; pB.SW = sR[s0][1][c - 1];
-            collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
-            store_site<T>(fout, g, y, x, cur, shift);
+            if constexpr (IsShifted<T>::value) {
+                collide_shifted(cur, pA, pB, ph, y, g.ny, flag);
+                store_site_sr<T>(fout, g, y, x, cur);
+            } else {
+                collide_site<true>(cur, pA, pB, ph, y, g.ny, flag);
+                store_site<T>(fout, g, y, x, cur, shift);
+            }
         }
     };
     for (int y = y0; y < y1; y += 2) {
