@@ -50,7 +50,8 @@ typedef enum {
     LBM_EINVAL = 1,     /* invalid argument or parameter set */
     LBM_ENOMEM = 2,     /* allocation failed or workspace too small */
     LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
-    LBM_EUNSTABLE = 4,  /* sticky: a NaN or negative density was seen by the step */
+    LBM_EUNSTABLE = 4,  /* sticky: a NaN or negative density was seen by the step (with 16-bit
+                         * storage: below -1 % (FP16) or -5 % (BF16) of the shift rho0_s) */
     LBM_ETIMEOUT = 5,   /* sticky: a bounded device-side wait gave up */
     LBM_ESTATE = 6,     /* call not valid in the handle's current state */
     LBM_EIO = 7         /* file I/O error (save/load) */
@@ -183,6 +184,12 @@ lbm_status lbm_get_populations(lbm_handle* h, double* host);
 /* Replace the state by the given post-streaming populations (2*9*ny*nx doubles,
  * host pointer), rounded to the storage type.  The step counter is kept. */
 lbm_status lbm_set_populations(lbm_handle* h, const double* host);
+
+/* The same two calls with FP32 host values (2*9*ny*nx floats, same layout): half
+ * the bytes over the host link, exact for FP32 storage (for 16-bit storage the
+ * values are rounded to it as above). */
+lbm_status lbm_get_populations_f32(lbm_handle* h, float* host);
+lbm_status lbm_set_populations_f32(lbm_handle* h, const float* host);
 
 /* Write the raw stored state (header + populations) to a file / read it back
  * into a handle created with the same nx, ny and storage.  Bitwise round trip. */

@@ -17,15 +17,15 @@ __device__ __forceinline__ void nbr_sum(const Nbr& r, float& sx, float& sy) {
 // Common velocity u = sum_s j_s / tau_s / sum_s rho_s / tau_s (Eq. 1) and the
 // accelerations a_s = F_s / rho_s: Shan-Chen coupling to the other component's
 // pseudopotential, the external (buoyancy, body) accelerations and, on the wall
-// rows, the fluid-boundary force.  Raises bit 0 of the guard flag for a negative
-// or non-finite density.
+// rows, the fluid-boundary force.  Raises bit 0 of the guard flag for a density
+// below ph.rho_floor (0 for FP32 storage) or a non-finite one.
 __device__ __forceinline__ void velocity_and_accel(const float rho[2], const float jx[2], const float jy[2],
                                                    const Nbr& psiA, const Nbr& psiB, const Physics& ph, int y,
                                                    int ny, int* flag, float& ux, float& uy, float ax[2],
                                                    float ay[2]) {
     const float rA = rho[0];
     const float rB = rho[1];
-    if (!(rA >= 0.0f && rB >= 0.0f && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
+    if (!(rA >= ph.rho_floor[0] && rB >= ph.rho_floor[1] && rA < 1e30f && rB < 1e30f)) atomicOr(flag, 1);
     const float inv = 1.0f / (rA * ph.om[0] + rB * ph.om[1]);
     ux = (jx[0] * ph.om[0] + jx[1] * ph.om[1]) * inv;
     uy = (jy[0] * ph.om[0] + jy[1] * ph.om[1]) * inv;

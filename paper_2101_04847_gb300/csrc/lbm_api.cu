@@ -531,6 +531,14 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     ph.ax_ext = (float)p->gx;
     ph.shift[0] = h->shift[0];
     ph.shift[1] = h->shift[1];
+    // The instability guard rejects negative densities.  16-bit storage cannot hold a
+    // pure phase exactly (h = -w rho0 is not on its grid), and its stochastic rounding
+    // makes the density of an absent component fluctuate around zero by a few units
+    // of the stored spacing: there the guard accepts down to -1 % (FP16) or -5 %
+    // (BF16) of rho0_s, far above the rounding noise and far below a real blow-up.
+    const float floor_frac = p->storage == LBM_STORE_F16 ? 0.01f : (p->storage == LBM_STORE_BF16 ? 0.05f : 0.0f);
+    ph.rho_floor[0] = -floor_frac * h->shift[0];
+    ph.rho_floor[1] = -floor_frac * h->shift[1];
     st = run_init(h);
     if (st != LBM_OK) {
         std::string msg = g_last_error;
@@ -680,6 +688,26 @@ lbm_status lbm_set_populations(lbm_handle* h, const double* host) {
     const size_t n = (size_t)18 * h->p.nx * h->p.ny;
     LBM_TRY(cudaMemcpyAsync(S, host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy populations");
     LBM_TRY(lbm::launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream), "push kernel");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations_f32(lbm_handle* h, float* host) {
+    if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+    float* S = reinterpret_cast<float*>(h->scratch());
+    LBM_TRY(lbm::launch_pull_to_float(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream), "pull kernel");
+    const size_t n = (size_t)18 * h->p.nx * h->p.ny;
+    LBM_TRY(cudaMemcpyAsync(host, S, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "copy populations");
+    LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations_f32(lbm_handle* h, const float* host) {
+    if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+    float* S = reinterpret_cast<float*>(h->scratch());
+    const size_t n = (size_t)18 * h->p.nx * h->p.ny;
+    LBM_TRY(cudaMemcpyAsync(S, host, n * sizeof(float), cudaMemcpyHostToDevice, h->stream), "copy populations");
+    LBM_TRY(lbm::launch_push_from_float(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream), "push kernel");
     LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
     return LBM_OK;
 }

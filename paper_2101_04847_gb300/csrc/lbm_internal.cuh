@@ -46,6 +46,7 @@ struct Physics {
     float ay_ext[2];   // buoyancy acceleration along y (per component)
     float ax_ext;      // body acceleration along x
     float shift[2];    // rho0_s of the shifted storage (0 for FP32)
+    float rho_floor[2];  // smallest density the instability guard accepts (see lbm_create)
 };
 
 // Geometry of one population array set.
@@ -121,6 +122,11 @@ cudaError_t launch_pull_to_double(const void* fin, const Grid& g, int storage,
 // stored state from S (double, [2][9][ny][nx])
 cudaError_t launch_push_from_double(const double* S, const Grid& g, int storage,
                                     const float shift[2], void* fout, cudaStream_t st);
+// the same with FP32 host-side values
+cudaError_t launch_pull_to_float(const void* fin, const Grid& g, int storage, const float shift[2], float* S,
+                                 cudaStream_t st);
+cudaError_t launch_push_from_float(const float* S, const Grid& g, int storage, const float shift[2], void* fout,
+                                   cudaStream_t st);
 
 // diagnostics (diag_kernels.cu)
 constexpr int kDiagTerms = 15;

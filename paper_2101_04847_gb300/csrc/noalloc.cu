@@ -157,6 +157,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in
     ph.ay_ext[1] = (float)(p->gravity_mode == 0 ? p->g : -p->g);
     ph.ax_ext = (float)p->gx;
     ph.shift[0] = ph.shift[1] = 0.0f;
+    ph.rho_floor[0] = ph.rho_floor[1] = 0.0f;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     e = cudaMemsetAsync(flag, 0, sizeof(int), st);   // the status word starts at zero on every call

@@ -874,8 +874,8 @@ __global__ void init_kernel(T* __restrict__ fout, Grid g, float sA, float sB, co
     store_site<T>(fout, g, y, x, f, shift);
 }
 
-template <typename T>
-__global__ void pull_to_double_kernel(const T* __restrict__ fin, Grid g, float sA, float sB, double* __restrict__ S) {
+template <typename T, typename V>
+__global__ void pull_to_host_kernel(const T* __restrict__ fin, Grid g, float sA, float sB, V* __restrict__ S) {
     const int x = blockIdx.x * kThreadsX + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
@@ -886,11 +886,11 @@ __global__ void pull_to_double_kernel(const T* __restrict__ fin, Grid g, float s
     pull_site<T>(fin, g, shift, y, x, xm, xp, f);
     const size_t n = (size_t)g.nx * g.ny;
     for (int s = 0; s < 2; ++s)
-        for (int i = 0; i < 9; ++i) S[(size_t)(s * 9 + i) * n + (size_t)y * g.nx + x] = (double)f[s][i];
+        for (int i = 0; i < 9; ++i) S[(size_t)(s * 9 + i) * n + (size_t)y * g.nx + x] = (V)f[s][i];
 }
 
-template <typename T>
-__global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, float sA, float sB, T* __restrict__ fout) {
+template <typename T, typename V>
+__global__ void push_from_host_kernel(const V* __restrict__ S, Grid g, float sA, float sB, T* __restrict__ fout) {
     const int x = blockIdx.x * kThreadsX + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
@@ -901,7 +901,7 @@ __global__ void push_from_double_kernel(const double* __restrict__ S, Grid g, fl
         for (int i = 0; i < 9; ++i) {
             const int ty = y + cy(i);
             const int tx = (x + cx(i) + g.nx) % g.nx;
-            const double v = (ty >= 0 && ty < g.ny)
+            const V v = (ty >= 0 && ty < g.ny)
                 ? S[(size_t)(s * 9 + i) * n + (size_t)ty * g.nx + tx]
                 : S[(size_t)(s * 9 + opp(i)) * n + (size_t)y * g.nx + x];
             f[s][i] = (float)v;
@@ -1011,36 +1011,57 @@ cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shif
     return cudaGetLastError();
 }
 
-cudaError_t launch_pull_to_double(const void* fin, const Grid& g, int storage, const float shift[2], double* S,
-                                  cudaStream_t st) {
+template <typename V>
+static cudaError_t launch_pull_to_host(const void* fin, const Grid& g, int storage, const float shift[2], V* S,
+                                       cudaStream_t st) {
     dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
     switch (storage) {
         case LBM_STORE_F16:
-            pull_to_double_kernel<__half><<<grid, kThreadsX, 0, st>>>((const __half*)fin, g, shift[0], shift[1], S);
+            pull_to_host_kernel<__half, V><<<grid, kThreadsX, 0, st>>>((const __half*)fin, g, shift[0], shift[1], S);
             break;
         case LBM_STORE_BF16:
-            pull_to_double_kernel<__nv_bfloat16><<<grid, kThreadsX, 0, st>>>((const __nv_bfloat16*)fin, g, shift[0], shift[1], S);
+            pull_to_host_kernel<__nv_bfloat16, V><<<grid, kThreadsX, 0, st>>>((const __nv_bfloat16*)fin, g, shift[0],
+                                                                              shift[1], S);
             break;
         default:
-            pull_to_double_kernel<float><<<grid, kThreadsX, 0, st>>>((const float*)fin, g, shift[0], shift[1], S);
+            pull_to_host_kernel<float, V><<<grid, kThreadsX, 0, st>>>((const float*)fin, g, shift[0], shift[1], S);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_push_from_double(const double* S, const Grid& g, int storage, const float shift[2], void* fout,
-                                    cudaStream_t st) {
+template <typename V>
+static cudaError_t launch_push_from_host(const V* S, const Grid& g, int storage, const float shift[2], void* fout,
+                                         cudaStream_t st) {
     dim3 grid((g.nx + kThreadsX - 1) / kThreadsX, g.ny);
     switch (storage) {
         case LBM_STORE_F16:
-            push_from_double_kernel<__half><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (__half*)fout);
+            push_from_host_kernel<__half, V><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (__half*)fout);
             break;
         case LBM_STORE_BF16:
-            push_from_double_kernel<__nv_bfloat16><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (__nv_bfloat16*)fout);
+            push_from_host_kernel<__nv_bfloat16, V><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1],
+                                                                                (__nv_bfloat16*)fout);
             break;
         default:
-            push_from_double_kernel<float><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (float*)fout);
+            push_from_host_kernel<float, V><<<grid, kThreadsX, 0, st>>>(S, g, shift[0], shift[1], (float*)fout);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_pull_to_double(const void* fin, const Grid& g, int storage, const float shift[2], double* S,
+                                  cudaStream_t st) {
+    return launch_pull_to_host(fin, g, storage, shift, S, st);
+}
+cudaError_t launch_push_from_double(const double* S, const Grid& g, int storage, const float shift[2], void* fout,
+                                    cudaStream_t st) {
+    return launch_push_from_host(S, g, storage, shift, fout, st);
+}
+cudaError_t launch_pull_to_float(const void* fin, const Grid& g, int storage, const float shift[2], float* S,
+                                 cudaStream_t st) {
+    return launch_pull_to_host(fin, g, storage, shift, S, st);
+}
+cudaError_t launch_push_from_float(const float* S, const Grid& g, int storage, const float shift[2], void* fout,
+                                   cudaStream_t st) {
+    return launch_push_from_host(S, g, storage, shift, fout, st);
 }
 
 }  // namespace lbm

@@ -65,6 +65,8 @@ _PROTOS = {
     "lbm_get_fields": (C.c_int, [_h, _dp, _dp, _dp, _dp]),
     "lbm_get_populations": (C.c_int, [_h, _dp]),
     "lbm_set_populations": (C.c_int, [_h, _dp]),
+    "lbm_get_populations_f32": (C.c_int, [_h, C.c_void_p]),
+    "lbm_set_populations_f32": (C.c_int, [_h, C.c_void_p]),
     "lbm_save": (C.c_int, [_h, C.c_char_p]),
     "lbm_load": (C.c_int, [_h, C.c_char_p]),
     "lbm_destroy": (None, [_h]),
@@ -245,16 +247,31 @@ class Solver:
         return out
 
     def populations(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Post-streaming populations (2, 9, ny, nx); float64 unless `out` is float32."""
         if out is None:
             out = np.empty((2, 9, self.ny, self.nx))
-        _check(self.lib.lbm_get_populations(self._h, _ptr(out)), "lbm_get_populations")
+        if out.shape != (2, 9, self.ny, self.nx) or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous array of shape (2, 9, {self.ny}, {self.nx})")
+        if out.dtype == np.float32:
+            _check(self.lib.lbm_get_populations_f32(self._h, out.ctypes.data), "lbm_get_populations_f32")
+        elif out.dtype == np.float64:
+            _check(self.lib.lbm_get_populations(self._h, _ptr(out)), "lbm_get_populations")
+        else:
+            raise ValueError("out must be float32 or float64")
         return out
 
     def set_populations(self, f: np.ndarray):
-        f = np.ascontiguousarray(f, dtype=np.float64)
+        """Replace the state; float32 arrays go through the FP32 entry point as they are."""
+        if f.dtype == np.float32:
+            f = np.ascontiguousarray(f)
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
         if f.shape != (2, 9, self.ny, self.nx):
             raise ValueError(f"populations must have shape (2, 9, {self.ny}, {self.nx})")
-        _check(self.lib.lbm_set_populations(self._h, _ptr(f)), "lbm_set_populations")
+        if f.dtype == np.float32:
+            _check(self.lib.lbm_set_populations_f32(self._h, f.ctypes.data), "lbm_set_populations_f32")
+        else:
+            _check(self.lib.lbm_set_populations(self._h, _ptr(f)), "lbm_set_populations")
 
     def save(self, path: str | Path):
         _check(self.lib.lbm_save(self._h, str(path).encode()), "lbm_save")

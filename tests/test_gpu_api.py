@@ -108,3 +108,20 @@ def test_runs_on_a_caller_stream(gpu):
     assert np.array_equal(a.populations(), b.populations())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_fp32_population_transfer_matches_the_fp64_one(gpu, storage):
+    # the FP32 entry points carry the same state as the float64 ones: both paths
+    # round the host values to FP32 before storing them, and the device computes
+    # the read-back values in FP32 in both
+    d = inputs.params(inputs.C0, nx=150, ny=40, crop_rows=3, g=1e-4)
+    f = inputs.random_populations(3, 150, 40, lo=0.02, hi=0.2)
+    with lbm.Solver(storage=storage, **d) as a, lbm.Solver(storage=storage, **d) as b:
+        a.set_populations(f)
+        b.set_populations(f.astype(np.float32))
+        a.step(5)
+        b.step(5)
+        ga, gb = a.populations(), b.populations(out=np.empty(f.shape, dtype=np.float32))
+        assert gb.dtype == np.float32
+        assert np.array_equal(ga, gb.astype(np.float64))
