@@ -281,7 +281,8 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
 /* Held-out run: fine run seeded `seed` (after warmup), coarse run started from its
  * restriction and corrected every interval by the network: use_net 0 = no
  * correction, 1 = densities and velocity, 2 = order parameter only (rho_A and rho_B
- * move by opposite amounts, velocity kept).  Corrections keep each component's
+ * move by opposite amounts, velocity kept), 3 = order parameter and a quarter of the
+ * velocity correction.  Corrections keep each component's
  * mass and never halve a density.  Diagnostics of both runs at intervals + 1 times
  * into coarse_out / fine_out (the fine run is the judge and the fallback: if the
  * coarse run turns unstable its status is returned, fine_out stays valid). */

@@ -366,10 +366,10 @@ __global__ void normalize_kernel(const float* __restrict__ raw, const float* __r
 
 // The density corrections of one site from the network output (drho_A, drho_B in
 // physical units), limited so that no density drops below half its value.
-// mode 1: drho_A and drho_B as predicted; mode 2: only the order parameter,
+// mode 1: drho_A and drho_B as predicted; modes 2 and 3: only the order parameter,
 // drho_A = -drho_B = (drho_A - drho_B) / 2, so the total density is unchanged.
 __device__ __forceinline__ void limited_drho(int mode, const double rho[2], double pA, double pB, double d[2]) {
-    if (mode == 2) {
+    if (mode >= 2) {
         const double h = fmin(fmax(0.5 * (pA - pB), -0.5 * rho[0]), 0.5 * rho[1]);
         d[0] = h;
         d[1] = -h;
@@ -409,8 +409,8 @@ __global__ void drho_sum_kernel(const double* __restrict__ S, const float* __res
 
 // Re-equilibration with the corrected moments: with rho'_s = rho_s + drho_s - mean
 // (drho limited as above, the mean over the grid removed so that each component's
-// mass is unchanged) and u' = u_b + du in mode 1, u' = u_b in mode 2 (u_b = j / rho
-// of S itself),
+// mass is unchanged) and u' = u_b + du in mode 1, u_b in mode 2 and u_b + du / 4 in
+// mode 3 (u_b = j / rho of S itself),
 //   f <- f^eq(rho'_s, u') + (rho'_s / rho_s) (f - f^eq(rho_s, u_b)),
 // i.e. the non-equilibrium part is kept in proportion to the density.
 __global__ void correct_kernel(double* __restrict__ S, const float* __restrict__ y, size_t n, float4 oscale,
@@ -430,7 +430,9 @@ __global__ void correct_kernel(double* __restrict__ S, const float* __restrict__
             }
         const double r = rho[0] + rho[1];
         const double ux = jx / r, uy = jy / r;
-        const double du = mode == 1 ? 1.0 : 0.0;   // mode 2 keeps the velocity
+        // mode 2 keeps the velocity; mode 3 relaxes it a quarter of the way (the full
+        // correction of mode 1 feeds back into the growing coarse modes)
+        const double du = mode == 1 ? 1.0 : (mode == 3 ? 0.25 : 0.0);
         const double vx = ux + du * (double)y[2 * n + k] * oscale.z, vy = uy + du * (double)y[3 * n + k] * oscale.w;
         double d[2];
         limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, d);
@@ -543,7 +545,7 @@ lbm_status set_coarse(lbm_closure* c, const float* fld) {
 }
 
 // apply the network's correction to the coarse run (mode 1: densities and velocity,
-// mode 2: order parameter only)
+// mode 2: order parameter only, mode 3: order parameter and a quarter of the velocity)
 lbm_status correct(lbm_closure* c, int mode) {
     CL_STATUS(coarse_fields(c, c->raw));
     lbm::normalize_kernel<<<512, 256, 0, c->stream>>>(c->raw, nullptr, c->nc, f4(c->in_mean), f4(c->in_scale),
@@ -793,7 +795,7 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
 lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out) {
     if (!c || intervals < 0 || warmup_fine_steps < 0 || !coarse_out || !fine_out) return cl_fail(LBM_EINVAL, "invalid arguments");
-    if (use_net < 0 || use_net > 2) return cl_fail(LBM_EINVAL, "use_net must be 0, 1 or 2");
+    if (use_net < 0 || use_net > 3) return cl_fail(LBM_EINVAL, "use_net must be 0, 1, 2 or 3");
     if (use_net && c->ntrain == 0) return cl_fail(LBM_ESTATE, "the network has not been trained");
     CL_STATUS(lbm::handle_reseed(c->fine, seed));
     CL_STATUS(lbm_step(c->fine, warmup_fine_steps));

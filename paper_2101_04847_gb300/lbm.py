@@ -383,7 +383,8 @@ class Closure:
         return loss.value
 
     def evaluate(self, seed: int, warmup: int, intervals: int, use_net: int) -> tuple[list[dict], list[dict]]:
-        """use_net: 0 no correction, 1 densities and velocity, 2 order parameter only."""
+        """use_net: 0 no correction, 1 densities and velocity, 2 order parameter only,
+        3 order parameter and a quarter of the velocity correction."""
         co = (LbmDiag * (intervals + 1))()
         fi = (LbmDiag * (intervals + 1))()
         _check(self.lib.lbm_closure_evaluate(self._c, seed, warmup, intervals, int(use_net), co, fi),
