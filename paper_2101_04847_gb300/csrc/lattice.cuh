@@ -135,6 +135,23 @@ __device__ __forceinline__ void store_site_sr(T* __restrict__ fout, const Grid& 
     }
 }
 
+// Store of a time step's result f: FP32 storage as it is; 16-bit storage as
+// h = f - w_i rho0_s with the stochastic rounding above.
+template <typename T>
+__device__ __forceinline__ void store_step(T* __restrict__ fout, const Grid& g, int y, int x, const float f[2][9],
+                                           const float shift[2]) {
+    if constexpr (IsShifted<T>::value) {
+        float h[2][9];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[s][i] = f[s][i] - wf(i) * shift[s];
+        store_site_sr<T>(fout, g, y, x, h);
+    } else {
+        store_site<T>(fout, g, y, x, f, shift);
+    }
+}
+
 __device__ __forceinline__ float sum9(const float* f) {
     return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
 }

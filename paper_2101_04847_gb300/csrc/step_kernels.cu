@@ -105,7 +105,7 @@ step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
             pB.NE = sR[s2][1][k + 1]; pB.NW = sR[s2][1][k - 1];
             pB.SE = sR[s0][1][k + 1]; pB.SW = sR[s0][1][k - 1];
             collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
-            store_site<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -298,7 +298,7 @@ __device__ __forceinline__ void warp_tile(const T* __restrict__ fin, T* __restri
         }
         if (owner) {
             collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
-            store_site<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
@@ -504,7 +504,7 @@ step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
         }
         if (owner) {
             collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
-            store_site<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
@@ -838,7 +838,7 @@ collide_kernel(const T* __restrict__ fin, const float* __restrict__ psi, T* __re
         }
     }
     collide_site<IsShifted<T>::value == false>(f, p[0], p[1], ph, y, g.ny, flag);
-    store_site<T>(fout, g, y, x, f, ph.shift);
+    store_step<T>(fout, g, y, x, f, ph.shift);
 }
 
 // ---------------------------------------------------------------------------
