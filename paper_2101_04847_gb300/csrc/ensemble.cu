@@ -53,7 +53,7 @@ void ens_drop_graphs(lbm_ensemble* e) {
 }
 
 int tiles_of(const lbm::Grid& g, int rows, int* tx, int* ty) {
-    *tx = (g.nx + 127) / 128;
+    *tx = (g.nx + lbm::kBlockTileW - 1) / lbm::kBlockTileW;
     *ty = std::min(g.ny, std::max(1, (g.ny + rows - 1) / rows));
     return *tx * *ty;
 }

@@ -86,7 +86,7 @@ Layout make_layout(const lbm_params& p) {
     // column 0 sits 128 bytes into each row; the row leaves room for the staged
     // kernel's windows (up to 144 columns from x0 - 10, x0 < nx) and the ghost copies
     L.origin = (int)(128 / elem_size(p.storage));
-    L.pitch = (L.origin + p.nx + 160 + 63) / 64 * 64;
+    L.pitch = (L.origin + p.nx + lbm::kBlockTileW + 32 + 63) / 64 * 64;
     L.plane = (size_t)p.ny * L.pitch;
     L.pop_bytes = 18 * L.plane * elem_size(p.storage);
     const size_t n = (size_t)p.nx * p.ny;

@@ -58,6 +58,9 @@ struct Grid {
     size_t plane;       // elements per (component, direction) plane = ny * pitch
 };
 
+// Columns of one block tile of the block-staged kernel (one thread per column).
+constexpr int kBlockTileW = 128;
+
 struct StepLaunch {
     const void* fin;
     void* fout;

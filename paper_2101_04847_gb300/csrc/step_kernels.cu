@@ -532,7 +532,7 @@ constexpr int kBlockStages = 5;   // rows y..y+2 in use + 2 rows prefetched (4 s
 template <typename T> struct BlockWin {
     // 132 columns plus the alignment slack of the window start, in 16-byte units
     static constexpr int kAlign = 16 / (int)sizeof(T);
-    static constexpr int value = (132 + kAlign - 1 + kAlign - 1) / kAlign * kAlign;
+    static constexpr int value = (kBlockTileW + 4 + kAlign - 1 + kAlign - 1) / kAlign * kAlign;
 };
 
 template <typename T>
@@ -568,7 +568,7 @@ __device__ __forceinline__ void pull_block(const T* __restrict__ stS, const T* _
 
 // Density ring of the block tile: slot 1 + t holds column x0 + t, slots 0 and 129
 // the halo columns x0 - 1 and x0 + 128.
-typedef float BlockRing[4][2][kThreadsX + 2];
+typedef float BlockRing[4][2][kBlockTileW + 2];
 
 // One block tile: columns [x0, x0 + 128) and rows [y0, y1) of one grid.  dsm: the
 // block_smem_bytes<T>() of dynamic shared memory (row stages, then the mbarriers).
@@ -591,8 +591,8 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     const int k = t + 2 + slack;
     // threads 64 / 65: the halo columns x0 - 1 / x0 + 128 (window columns 1 / 130 + slack)
     const bool halo = t == 64 || t == 65;
-    const int kh = t == 64 ? 1 + slack : 130 + slack;
-    const int sh = t == 64 ? 0 : kThreadsX + 1;
+    const int kh = t == 64 ? 1 + slack : kBlockTileW + 2 + slack;
+    const int sh = t == 64 ? 0 : kBlockTileW + 1;
     const T* win = fin + (e0 - slack);
     const float shift[2] = {ph.shift[0], ph.shift[1]};
     const uint32_t row_bytes = W * sizeof(T);
@@ -710,13 +710,13 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
 // One grid: block (bx, by) takes columns [128 bx, 128 bx + 128) and the by-th of
 // gridDim.y tiles of (nearly) equal height.
 template <typename T>
-__global__ void __launch_bounds__(kThreadsX, 4)
+__global__ void __launch_bounds__(kBlockTileW, 512 / kBlockTileW)
 step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ BlockRing sR;
     const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
     const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
-    block_tile<T>(fin, fout, g, ph, blockIdx.x * kThreadsX, y0, y1, dsm, sR, flag);
+    block_tile<T>(fin, fout, g, ph, blockIdx.x * kBlockTileW, y0, y1, dsm, sR, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -726,7 +726,7 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
 // the member's grid, physics and storage type; no member waits for another, so
 // uneven grids need no barrier.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsX, 4)
+__global__ void __launch_bounds__(kBlockTileW, 512 / kBlockTileW)
 ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ BlockRing sR;
@@ -746,15 +746,15 @@ ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     void* fout = M.buf[parity ^ 1];
     switch (M.storage) {
         case LBM_STORE_F16:
-            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, tx * kThreadsX, y0, y1, dsm, sR,
+            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, tx * kBlockTileW, y0, y1, dsm, sR,
                                M.flag);
             break;
         case LBM_STORE_BF16:
             block_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, M.phys,
-                                      tx * kThreadsX, y0, y1, dsm, sR, M.flag);
+                                      tx * kBlockTileW, y0, y1, dsm, sR, M.flag);
             break;
         default:
-            block_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, tx * kThreadsX, y0, y1, dsm, sR,
+            block_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, tx * kBlockTileW, y0, y1, dsm, sR,
                               M.flag);
     }
 }
@@ -770,7 +770,8 @@ int ensemble_slots(size_t smem, cudaError_t* err) {
                                          (int)block_smem_bytes<float>());
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel, kThreadsX, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel, kBlockTileW, smem);
     if (err) *err = e;
     return std::max(1, sms * occ);
 }
@@ -785,7 +786,7 @@ cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_ti
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    ensemble_step_kernel<<<total_tiles, kThreadsX, smem, st>>>(d_members, n, parity);
+    ensemble_step_kernel<<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
     return cudaGetLastError();
 }
 
@@ -943,14 +944,14 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
             int dev = 0, sms = 0, occ = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_block_kernel<T>, kThreadsX, smem)) !=
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_block_kernel<T>, kBlockTileW, smem)) !=
                 cudaSuccess)
                 return e;
             tiles_auto = std::max(1, sms * occ);
         }
-        const int gx = (g.nx + kThreadsX - 1) / kThreadsX;
+        const int gx = (g.nx + kBlockTileW - 1) / kBlockTileW;
         dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, tiles_auto));
-        step_block_kernel<T><<<grid, kThreadsX, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, L.flag);
+        step_block_kernel<T><<<grid, kBlockTileW, smem, st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, L.flag);
     } else if (kernel == LBM_KERNEL_PIPE) {
         const int ty = L.tile_y > 0 ? L.tile_y : 32;
         const size_t smem = pipe_smem_bytes<T>();
