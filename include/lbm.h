@@ -66,8 +66,9 @@ typedef enum {
 typedef enum {
     LBM_KERNEL_FUSED = 0,    /* one fused pull stream-collide kernel per step (global-memory pulls) */
     LBM_KERNEL_TWO_PASS = 1, /* density kernel + stream-collide kernel per step */
-    LBM_KERNEL_STAGED = 2,   /* fused kernel, rows staged in shared memory by bulk async copies, block-wide sweep */
-    LBM_KERNEL_WARP = 3,     /* as STAGED, one independent sweep per warp (the ensemble's tile kernel) */
+    LBM_KERNEL_STAGED = 2,   /* fused kernel, rows staged in shared memory by bulk async copies,
+                              * block-wide sweep (the default: the fastest; the ensemble's tile code) */
+    LBM_KERNEL_WARP = 3,     /* as STAGED, one independent sweep per warp */
     LBM_KERNEL_PIPE = 4      /* as STAGED, warps sweep independently over shared stages (no block barrier) */
 } lbm_kernel;
 

@@ -110,6 +110,7 @@ lbm_status ens_build_table(lbm_ensemble* e) {
         m.buf[1] = lbm::handle_buffer(h, 1);
         m.flag = lbm::handle_flag(h);
         m.storage = lbm::handle_params(h).storage;
+        m.step_ctr = lbm::handle_step_counters(h);
         const int tiles = tiles_of(m.grid, e->rows, &m.tiles_x, &m.tiles_y);
         m.tile_begin = begin;
         begin += tiles;

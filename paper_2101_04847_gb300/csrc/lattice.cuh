@@ -85,11 +85,12 @@ __device__ __forceinline__ void store_site(T* __restrict__ fout, const Grid& g, 
 // magnitude with probability equal to its distance from the lower neighbour, in
 // units of the spacing: uniform random bits are added below the kept mantissa of
 // the FP32 pattern and the sum is truncated.  The random bits are a hash of the
-// site, the component and the unrounded rest population (lowbias32 of C.
-// Wellons' hash prospector), stepped by the PCG multiplier of M. E. O'Neill per
-// value, so a state and its update always round the same way (results are
-// reproducible) while any change of the state changes the rounding.  FP16
-// subnormals (|h| < 2^-14) keep a truncation bias below 2^-24.
+// site, the component and the time step (lowbias32 of C. Wellons' hash
+// prospector; a counter-based generator, so results are reproducible), stepped
+// by the PCG multiplier of M. E. O'Neill per value.  The time step matters: a
+// hash of the values alone repeats its decisions in slowly varying regions and
+// drifts the masses by ~1e-4 per 5000 steps.  FP16 subnormals (|h| < 2^-14) keep
+// a truncation bias below 2^-24.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t hash_lowbias32(uint32_t x) {
     x ^= x >> 16;
@@ -99,6 +100,15 @@ __device__ __forceinline__ uint32_t hash_lowbias32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
+// Seed of a launch's stochastic rounding: a hash of its time step (0 without a counter).
+__device__ __forceinline__ uint32_t launch_seed(const Physics& ph) {
+    return ph.step_in ? hash_lowbias32(*ph.step_in * 0x9E3779B9u + 0x7F4A7C15u) : 0u;
+}
+// The one thread `leader` of a launch passes the time step on to the next launch.
+__device__ __forceinline__ void advance_step(const Physics& ph, bool leader) {
+    if (leader && ph.step_out) *ph.step_out = *ph.step_in + 1u;
+}
+
 template <typename T> __device__ __forceinline__ T round_stochastic(float v, uint32_t r);
 template <> __device__ __forceinline__ __half round_stochastic<__half>(float v, uint32_t r) {
     return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));   // 13 bits dropped
@@ -112,13 +122,13 @@ template <> __device__ __forceinline__ __nv_bfloat16 round_stochastic<__nv_bfloa
 // copy of the two first / last columns.
 template <typename T>
 __device__ __forceinline__ void store_site_sr(T* __restrict__ fout, const Grid& g, int y, int x,
-                                              const float h[2][9]) {
+                                              const float h[2][9], uint32_t seed) {
     T* q = fout + (size_t)y * g.pitch + g.origin + x;
     T tv[2][9];
     const uint32_t site = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        uint32_t r = hash_lowbias32((site * 2u + (uint32_t)s) ^ __float_as_uint(h[s][0]));
+        uint32_t r = hash_lowbias32((site * 2u + (uint32_t)s) ^ seed);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             r = r * 747796405u + 2891336453u;
@@ -139,14 +149,14 @@ __device__ __forceinline__ void store_site_sr(T* __restrict__ fout, const Grid& 
 // h = f - w_i rho0_s with the stochastic rounding above.
 template <typename T>
 __device__ __forceinline__ void store_step(T* __restrict__ fout, const Grid& g, int y, int x, const float f[2][9],
-                                           const float shift[2]) {
+                                           const float shift[2], uint32_t seed) {
     if constexpr (IsShifted<T>::value) {
         float h[2][9];
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int i = 0; i < 9; ++i) h[s][i] = f[s][i] - wf(i) * shift[s];
-        store_site_sr<T>(fout, g, y, x, h);
+        store_site_sr<T>(fout, g, y, x, h, seed);
     } else {
         store_site<T>(fout, g, y, x, f, shift);
     }

@@ -155,6 +155,9 @@ struct lbm_handle {
     void* pops(int k) { return ws + L.pops[k]; }
     double* scratch() { return (double*)(ws + L.scratch); }
     int* flag() { return (int*)(ws + L.flag); }
+    // the two time-step counters of the stochastic rounding (after the flag, same region)
+    uint32_t* step_ctr() { return (uint32_t*)(ws + L.flag) + 2; }
+    uint32_t saved_ctr[2] = {0, 0};   // counters kept with a saved state (tuning)
 };
 
 namespace {
@@ -167,6 +170,8 @@ lbm::StepLaunch step_launch(lbm_handle* h, int from) {
     S.flag = h->flag();
     S.grid = h->grid;
     S.phys = h->phys;
+    S.phys.step_in = h->step_ctr() + from;
+    S.phys.step_out = h->step_ctr() + (from ^ 1);
     S.storage = h->p.storage;
     S.tile_y = h->p.tile_y;
     return S;
@@ -274,6 +279,7 @@ int handle_parity(lbm_handle* h) { return h->cur; }
 Grid handle_grid(lbm_handle* h) { return h->grid; }
 Physics handle_phys(lbm_handle* h) { return h->phys; }
 int* handle_flag(lbm_handle* h) { return h->flag(); }
+uint32_t* handle_step_counters(lbm_handle* h) { return h->step_ctr(); }
 const lbm_params& handle_params(lbm_handle* h) { return h->p; }
 void handle_set_ensemble(lbm_handle* h, bool on) { h->in_ensemble = on; }
 void handle_advance(lbm_handle* h, int64_t n) {
@@ -283,9 +289,17 @@ void handle_advance(lbm_handle* h, int64_t n) {
 lbm_status handle_check(lbm_handle* h) { return check_flag(h); }
 // copy the current population buffer to the scratch region / back (state kept while tuning)
 cudaError_t handle_save_state(lbm_handle* h) {
+    cudaError_t e = cudaMemcpyAsync(h->saved_ctr, h->step_ctr(), sizeof(h->saved_ctr), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(h->scratch(), h->pops(h->cur), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
 }
 cudaError_t handle_restore_state(lbm_handle* h) {
+    cudaError_t e = cudaMemcpyAsync(h->step_ctr(), h->saved_ctr, sizeof(h->saved_ctr), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(h->pops(h->cur), h->scratch(), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
 }
 // rho_A, rho_B and the physical velocity on the whole grid (doubles in the scratch
@@ -446,7 +460,7 @@ lbm_status lbm_params_default(lbm_params* p) {
     p->y0 = -1.0;
     p->crop_rows = 10;
     p->storage = LBM_STORE_F32;
-    p->kernel = LBM_KERNEL_FUSED;
+    p->kernel = LBM_KERNEL_STAGED;
     p->tile_y = 0;
     return LBM_OK;
 }
@@ -539,6 +553,8 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     const float floor_frac = p->storage == LBM_STORE_F16 ? 0.01f : (p->storage == LBM_STORE_BF16 ? 0.05f : 0.0f);
     ph.rho_floor[0] = -floor_frac * h->shift[0];
     ph.rho_floor[1] = -floor_frac * h->shift[1];
+    ph.step_in = nullptr;    // set per launch (step_launch)
+    ph.step_out = nullptr;
     st = run_init(h);
     if (st != LBM_OK) {
         std::string msg = g_last_error;
@@ -763,6 +779,10 @@ lbm_status lbm_load(lbm_handle* h, const char* path) {
     std::fclose(f);
     if (!ok) return fail(LBM_EIO, "truncated state file");
     LBM_TRY(cudaMemcpyAsync(h->pops(h->cur), buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream), "copy state");
+    // the rounding counter continues from the saved step, as in the run that saved it
+    h->saved_ctr[0] = h->saved_ctr[1] = (uint32_t)hd.step;
+    LBM_TRY(cudaMemcpyAsync(h->step_ctr(), h->saved_ctr, sizeof(h->saved_ctr), cudaMemcpyHostToDevice, h->stream),
+            "set step counter");
     LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
     h->step = hd.step;
     return LBM_OK;

@@ -47,6 +47,11 @@ struct Physics {
     float ax_ext;      // body acceleration along x
     float shift[2];    // rho0_s of the shifted storage (0 for FP32)
     float rho_floor[2];  // smallest density the instability guard accepts (see lbm_create)
+    // Time-step counter of the stochastic rounding: a launch reads *step_in and one of
+    // its threads writes *step_in + 1 to *step_out, the counter the next launch reads
+    // (two counters alternating with the buffers).  Null: no counter (seed 0).
+    const uint32_t* step_in;
+    uint32_t* step_out;
 };
 
 // Geometry of one population array set.
@@ -79,6 +84,7 @@ struct EnsMember {
     void* buf[2];        // the two population buffers (input = buf[parity])
     int* flag;           // the member's guard flag
     int storage;         // lbm_storage
+    uint32_t* step_ctr;  // the member's two time-step counters (see Physics)
     int tiles_x;         // block tiles along x (128 columns each)
     int tiles_y;         // block tiles along y (rows split evenly)
     int tile_begin;      // index of the member's first tile in the flat list
@@ -100,6 +106,7 @@ int handle_parity(lbm_handle* h);
 Grid handle_grid(lbm_handle* h);
 Physics handle_phys(lbm_handle* h);
 int* handle_flag(lbm_handle* h);
+uint32_t* handle_step_counters(lbm_handle* h);
 const lbm_params& handle_params(lbm_handle* h);
 void handle_set_ensemble(lbm_handle* h, bool on);
 void handle_advance(lbm_handle* h, int64_t n);

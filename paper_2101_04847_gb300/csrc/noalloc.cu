@@ -158,6 +158,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in
     ph.ax_ext = (float)p->gx;
     ph.shift[0] = ph.shift[1] = 0.0f;
     ph.rho_floor[0] = ph.rho_floor[1] = 0.0f;
+    ph.step_in = nullptr;
+    ph.step_out = nullptr;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     e = cudaMemsetAsync(flag, 0, sizeof(int), st);   // the status word starts at zero on every call

@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(kThreadsX)
 step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
     __shared__ float sR[4][2][kThreadsX + 2];
     const int t = threadIdx.x;
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && t == 0);
     const int x0 = blockIdx.x * kThreadsX;
     const int w = min(kThreadsX, g.nx - x0);
     const int y0 = blockIdx.y * tile_y;
@@ -105,7 +107,7 @@ step_fused_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
             pB.NE = sR[s2][1][k + 1]; pB.NW = sR[s2][1][k - 1];
             pB.SE = sR[s0][1][k + 1]; pB.SW = sR[s0][1][k - 1];
             collide_site<IsShifted<T>::value == false>(cur, pA, pB, ph, y, g.ny, flag);
-            store_step<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift, seed);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -207,7 +209,7 @@ __device__ __forceinline__ void pull_staged(const T* __restrict__ stS, const T* 
 template <typename T>
 __device__ __forceinline__ void warp_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
                                           const Physics& ph, int tile_y, int tx, int ty, unsigned char* my,
-                                          int* flag) {
+                                          uint32_t seed, int* flag) {
     constexpr int W = WinW<T>::value;
     const int lane = threadIdx.x & 31;
     uint64_t* bar = reinterpret_cast<uint64_t*>(my);
@@ -298,7 +300,7 @@ __device__ __forceinline__ void warp_tile(const T* __restrict__ fin, T* __restri
         }
         if (owner) {
             collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
-            store_step<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift, seed);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
@@ -316,9 +318,11 @@ step_warp_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
     extern __shared__ __align__(128) unsigned char dsm[];
     const int warp = threadIdx.x >> 5;
     const int tile = blockIdx.x * kWarpsPerBlock + warp;
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && threadIdx.x == 0);
     if (tile >= tiles) return;                      // whole warp leaves together
     warp_tile<T>(fin, fout, g, ph, tile_y, tile % tiles_x, tile / tiles_x,
-                 dsm + (size_t)warp * warp_smem_bytes<T>(), flag);
+                 dsm + (size_t)warp * warp_smem_bytes<T>(), seed, flag);
 }
 
 // warp tiles of one grid for the per-warp kernel
@@ -391,6 +395,8 @@ __device__ __forceinline__ void pull_pipe(const T* __restrict__ stS, const T* __
 template <typename T>
 __global__ void __launch_bounds__(kThreadsX, 4)
 step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int tile_y, int* flag) {
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     constexpr int S = kPipeStages;
     extern __shared__ __align__(128) unsigned char dsm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
@@ -504,7 +510,7 @@ step_pipe_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physic
         }
         if (owner) {
             collide_site<IsShifted<T>::value == false>(cur, p[0], p[1], ph, y, g.ny, flag);
-            store_step<T>(fout, g, y, x, cur, shift);
+            store_step<T>(fout, g, y, x, cur, shift, seed);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) { rm[s] = rc[s]; rc[s] = rp[s]; }
@@ -575,7 +581,7 @@ typedef float BlockRing[4][2][kBlockTileW + 2];
 template <typename T>
 __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
                                            const Physics& ph, int x0, int y0, int y1, unsigned char* dsm,
-                                           BlockRing& sR, int* flag) {
+                                           BlockRing& sR, uint32_t seed, int* flag) {
     constexpr int W = BlockWin<T>::value;
     constexpr int kAlign = BlockWin<T>::kAlign;
     T* stage = reinterpret_cast<T*>(dsm);
@@ -694,7 +700,7 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
             pB.SE = sR[s0][1][c + 1]; pB.SW = sR[s0][1][c - 1];
             if constexpr (IsShifted<T>::value) {
                 collide_shifted(cur, pA, pB, ph, y, g.ny, flag);
-                store_site_sr<T>(fout, g, y, x, cur);
+                store_site_sr<T>(fout, g, y, x, cur, seed);
             } else {
                 collide_site<true>(cur, pA, pB, ph, y, g.ny, flag);
                 store_site<T>(fout, g, y, x, cur, shift);
@@ -716,7 +722,9 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
     __shared__ BlockRing sR;
     const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
     const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
-    block_tile<T>(fin, fout, g, ph, blockIdx.x * kBlockTileW, y0, y1, dsm, sR, flag);
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+    block_tile<T>(fin, fout, g, ph, blockIdx.x * kBlockTileW, y0, y1, dsm, sR, seed, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -744,18 +752,23 @@ ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     const int y1 = (int)(((long long)(ty + 1) * M.grid.ny) / M.tiles_y);
     const void* fin = M.buf[parity];
     void* fout = M.buf[parity ^ 1];
+    Physics ph = M.phys;   // the member's counters, read / written as this parity dictates
+    ph.step_in = M.step_ctr + parity;
+    ph.step_out = M.step_ctr + (parity ^ 1);
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, local == 0 && threadIdx.x == 0);
     switch (M.storage) {
         case LBM_STORE_F16:
-            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, M.phys, tx * kBlockTileW, y0, y1, dsm, sR,
-                               M.flag);
+            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, ph, tx * kBlockTileW, y0, y1, dsm, sR,
+                               seed, M.flag);
             break;
         case LBM_STORE_BF16:
-            block_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, M.phys,
-                                      tx * kBlockTileW, y0, y1, dsm, sR, M.flag);
+            block_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph,
+                                      tx * kBlockTileW, y0, y1, dsm, sR, seed, M.flag);
             break;
         default:
-            block_tile<float>((const float*)fin, (float*)fout, M.grid, M.phys, tx * kBlockTileW, y0, y1, dsm, sR,
-                              M.flag);
+            block_tile<float>((const float*)fin, (float*)fout, M.grid, ph, tx * kBlockTileW, y0, y1, dsm, sR,
+                              seed, M.flag);
     }
 }
 
@@ -813,6 +826,8 @@ collide_kernel(const T* __restrict__ fin, const float* __restrict__ psi, T* __re
                Grid g, Physics ph, int* flag) {
     const int x = blockIdx.x * kThreadsX + threadIdx.x;
     const int y = blockIdx.y;
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     if (x >= g.nx) return;
     const int xm = x == 0 ? g.nx - 1 : x - 1;
     const int xp = x == g.nx - 1 ? 0 : x + 1;
@@ -839,7 +854,7 @@ collide_kernel(const T* __restrict__ fin, const float* __restrict__ psi, T* __re
         }
     }
     collide_site<IsShifted<T>::value == false>(f, p[0], p[1], ph, y, g.ny, flag);
-    store_step<T>(fout, g, y, x, f, ph.shift);
+    store_step<T>(fout, g, y, x, f, ph.shift, seed);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,7 +36,7 @@ def test_defaults(lib):
     p = lbm.default_params()
     assert (p.nx, p.ny) == (128, 256)
     assert (p.tau_A, p.tau_B, p.G, p.mass_A, p.mass_B, p.g) == (1.0, 1.0, 1.4, 1.0, 0.9, 1e-5)
-    assert (p.n_modes, p.amp, p.width, p.crop_rows, p.storage, p.kernel) == (8, 2.0, 1.5, 10, 0, 0)
+    assert (p.n_modes, p.amp, p.width, p.crop_rows, p.storage, p.kernel) == (8, 2.0, 1.5, 10, 0, lbm.KERNEL["staged"])
 
 
 def test_workspace_grows_with_the_grid(lib):
