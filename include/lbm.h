@@ -114,7 +114,8 @@ typedef struct {
     double viscous;      /* <u . div(eta grad u + eta grad u^T)>, eta = rho_bar cs^2 (tau - 1/2) */
     double enstrophy;    /* (1/2) sum omega^2 over the sub-domain */
     double rho_bar;      /* <rho> */
-    double h;            /* mixing-layer width 6 sum_y c (1 - c) of the normalised row-mean phi */
+    double h;            /* mixing-layer width 6 sum_y c (1 - c), c the row mean of the mass
+                          * fraction rho_A / (rho_A + rho_B) normalised by its two bulk values */
     double L_int;        /* interface length, 4-direction Cauchy-Crofton estimate */
     int64_t cc[4];       /* sign changes of (phi > 0) along 0, 90, 45, 135 degrees */
     int32_t status;      /* LBM_OK or LBM_EUNSTABLE */
@@ -283,7 +284,9 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
  * restriction and corrected every interval by the network: use_net 0 = no
  * correction, 1 = densities and velocity, 2 = order parameter only (rho_A and rho_B
  * move by opposite amounts, velocity kept), 3 = order parameter and a quarter of the
- * velocity correction.  Corrections keep each component's
+ * velocity correction, 4 = as 3 with the order-parameter correction (and the mass
+ * restoring offset) weighted by 4 c (1 - c) of the normalised mass fraction c, i.e.
+ * applied on the interface and not in either bulk.  Corrections keep each component's
  * mass and never halve a density.  Diagnostics of both runs at intervals + 1 times
  * into coarse_out / fine_out (the fine run is the judge and the fallback: if the
  * coarse run turns unstable its status is returned, fine_out stays valid). */

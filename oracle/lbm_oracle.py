@@ -310,10 +310,18 @@ def bulk_order_parameter(p: Params) -> tuple[float, float]:
     return p.mass_A - eps * p.mass_B, eps * p.mass_A - p.mass_B
 
 
-def mixing_width(phi_rows: np.ndarray, p: Params) -> float:
-    """h = 6 sum_y cbar (1 - cbar), cbar = (phibar - phi_bot) / (phi_top - phi_bot) clamped to [0, 1]."""
-    top, bot = bulk_order_parameter(p)
-    c = np.clip((phi_rows - bot) / (top - bot), 0.0, 1.0)
+def bulk_mass_fraction(p: Params) -> tuple[float, float]:
+    """c = rho_A / (rho_A + rho_B) in the pure top (A) and pure bottom (B) bulk of the initial state."""
+    eps = p.minority
+    return p.mass_A / (p.mass_A + eps * p.mass_B), eps * p.mass_A / (eps * p.mass_A + p.mass_B)
+
+
+def mixing_width(c_rows: np.ndarray, p: Params) -> float:
+    """h = 6 sum_y ct (1 - ct), ct = (cbar - c_bot) / (c_top - c_bot) clamped to [0, 1], cbar the row
+    means of the mass fraction c = rho_A / (rho_A + rho_B).  The mass fraction, unlike rho_A - rho_B,
+    keeps its bulk values when gravity compresses a tall column."""
+    top, bot = bulk_mass_fraction(p)
+    c = np.clip((c_rows - bot) / (top - bot), 0.0, 1.0)
     return float(6.0 * np.sum(c * (1.0 - c)))
 
 
@@ -407,14 +415,16 @@ def field_diagnostics(rhoA: np.ndarray, rhoB: np.ndarray, ux: np.ndarray, uy: np
 
     counts = cauchy_crofton_counts(phi, r0, r1)
     phi_rows = phi[R].mean(axis=1)
+    c = np.divide(rhoA, rho, out=np.zeros_like(rho), where=rho > 0.0)
+    c_rows = c[R].mean(axis=1)
     return dict(
         E_k=mean(0.5 * rho * (ux * ux + uy * uy)),
         E_p=p.g * mean(y * phi),
         buoyancy=p.g * mean(uy * phi),
         flux_pb=flux_pb, flux_K=flux_K, flux_tau=flux_tau,
         viscous=viscous, enstrophy=enstrophy, rho_bar=rho_bar, eta=eta,
-        h=mixing_width(phi_rows, p), L_int=cauchy_crofton_length(counts),
-        cc=counts, phi_rows=phi_rows,
+        h=mixing_width(c_rows, p), L_int=cauchy_crofton_length(counts),
+        cc=counts, phi_rows=phi_rows, c_rows=c_rows,
     )
 
 

@@ -367,10 +367,13 @@ __global__ void normalize_kernel(const float* __restrict__ raw, const float* __r
 // The density corrections of one site from the network output (drho_A, drho_B in
 // physical units), limited so that no density drops below half its value.
 // mode 1: drho_A and drho_B as predicted; modes 2 and 3: only the order parameter,
-// drho_A = -drho_B = (drho_A - drho_B) / 2, so the total density is unchanged.
-__device__ __forceinline__ void limited_drho(int mode, const double rho[2], double pA, double pB, double d[2]) {
+// drho_A = -drho_B = (drho_A - drho_B) / 2, so the total density is unchanged;
+// mode 4: the order parameter times the interface weight w (below).
+__device__ __forceinline__ void limited_drho(int mode, const double rho[2], double pA, double pB, double w,
+                                             double d[2]) {
     if (mode >= 2) {
-        const double h = fmin(fmax(0.5 * (pA - pB), -0.5 * rho[0]), 0.5 * rho[1]);
+        const double s = mode == 4 ? w : 1.0;
+        const double h = fmin(fmax(0.5 * s * (pA - pB), -0.5 * rho[0]), 0.5 * rho[1]);
         d[0] = h;
         d[1] = -h;
     } else {
@@ -379,20 +382,32 @@ __device__ __forceinline__ void limited_drho(int mode, const double rho[2], doub
     }
 }
 
+// Interface weight w = 4 c (1 - c) of the normalised mass fraction
+// c = (rho_A / rho - c_bot) / (c_top - c_bot), clamped to [0, 1]: 1 on the interface,
+// 0 in either bulk, so that mode 4 leaves the bulk composition alone.
+__device__ __forceinline__ double interface_weight(const double rho[2], double2 cbulk) {
+    const double r = rho[0] + rho[1];
+    if (!(r > 0.0)) return 0.0;
+    const double c = fmin(fmax((rho[0] / r - cbulk.y) / (cbulk.x - cbulk.y), 0.0), 1.0);
+    return 4.0 * c * (1.0 - c);
+}
+
 // sums of the limited density corrections (per block partials, fixed order); the
 // densities come from the populations S of the coarse run
+// (mode 4: the sum of the order-parameter corrections and the sum of the weights)
 __global__ void drho_sum_kernel(const double* __restrict__ S, const float* __restrict__ y, size_t n, float4 oscale,
-                                int mode, double* __restrict__ part) {
+                                int mode, double2 cbulk, double* __restrict__ part) {
     __shared__ double red[2][8];
     double a = 0.0, b = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         double rho[2] = {0.0, 0.0};
         for (int s = 0; s < 2; ++s)
             for (int i = 0; i < 9; ++i) rho[s] += S[(size_t)(s * 9 + i) * n + k];
+        const double w = interface_weight(rho, cbulk);
         double d[2];
-        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, d);
+        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, w, d);
         a += d[0];
-        b += d[1];
+        b += mode == 4 ? w : d[1];
     }
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, off);
@@ -409,14 +424,16 @@ __global__ void drho_sum_kernel(const double* __restrict__ S, const float* __res
 
 // Re-equilibration with the corrected moments: with rho'_s = rho_s + drho_s - mean
 // (drho limited as above, the mean over the grid removed so that each component's
-// mass is unchanged) and u' = u_b + du in mode 1, u_b in mode 2 and u_b + du / 4 in
-// mode 3 (u_b = j / rho of S itself),
+// mass is unchanged; mode 4 removes it in proportion to the interface weight,
+// drho_A = -drho_B = h - w sum(h) / sum(w)) and u' = u_b + du in mode 1, u_b in
+// mode 2 and u_b + du / 4 in modes 3 and 4 (u_b = j / rho of S itself),
 //   f <- f^eq(rho'_s, u') + (rho'_s / rho_s) (f - f^eq(rho_s, u_b)),
 // i.e. the non-equilibrium part is kept in proportion to the density.
 __global__ void correct_kernel(double* __restrict__ S, const float* __restrict__ y, size_t n, float4 oscale,
-                               int mode, const double* __restrict__ part, int nparts) {
+                               int mode, double2 cbulk, const double* __restrict__ part, int nparts) {
     double mA = 0.0, mB = 0.0;
     for (int p = 0; p < nparts; ++p) { mA += part[2 * p]; mB += part[2 * p + 1]; }
+    const double hw = mode == 4 && mB > 0.0 ? mA / mB : 0.0;   // mode 4: sum(h) / sum(w)
     mA /= (double)n;
     mB /= (double)n;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
@@ -430,14 +447,20 @@ __global__ void correct_kernel(double* __restrict__ S, const float* __restrict__
             }
         const double r = rho[0] + rho[1];
         const double ux = jx / r, uy = jy / r;
-        // mode 2 keeps the velocity; mode 3 relaxes it a quarter of the way (the full
-        // correction of mode 1 feeds back into the growing coarse modes)
-        const double du = mode == 1 ? 1.0 : (mode == 3 ? 0.25 : 0.0);
+        // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
+        // full correction of mode 1 feeds back into the growing coarse modes)
+        const double du = mode == 1 ? 1.0 : (mode >= 3 ? 0.25 : 0.0);
         const double vx = ux + du * (double)y[2 * n + k] * oscale.z, vy = uy + du * (double)y[3 * n + k] * oscale.w;
+        const double w = interface_weight(rho, cbulk);
         double d[2];
-        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, d);
-        d[0] -= mA;
-        d[1] -= mB;
+        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, w, d);
+        if (mode == 4) {
+            d[0] -= w * hw;
+            d[1] = -d[0];
+        } else {
+            d[0] -= mA;
+            d[1] -= mB;
+        }
         for (int s = 0; s < 2; ++s) {
             const double r0 = rho[s];
             if (!(r0 > 0.0)) continue;
@@ -545,17 +568,22 @@ lbm_status set_coarse(lbm_closure* c, const float* fld) {
 }
 
 // apply the network's correction to the coarse run (mode 1: densities and velocity,
-// mode 2: order parameter only, mode 3: order parameter and a quarter of the velocity)
+// mode 2: order parameter only, mode 3: order parameter and a quarter of the velocity,
+// mode 4: as mode 3 with the order parameter corrected on the interface only)
 lbm_status correct(lbm_closure* c, int mode) {
+    // bulk mass fractions of the coarse run's initial state (pure A on top, pure B below)
+    const lbm_params& q = c->coarse_p;
+    const double2 cbulk = make_double2(q.mass_A / (q.mass_A + q.minority * q.mass_B),
+                                       q.minority * q.mass_A / (q.minority * q.mass_A + q.mass_B));
     CL_STATUS(coarse_fields(c, c->raw));
     lbm::normalize_kernel<<<512, 256, 0, c->stream>>>(c->raw, nullptr, c->nc, f4(c->in_mean), f4(c->in_scale),
                                                       f4(c->out_scale), c->xin, nullptr);
     CL_TRY(cudaGetLastError(), "normalize");
     CL_TRY(lbm::cnn::forward(c->net, c->params, c->xin, c->yout, c->stream), "cnn forward");
     CL_TRY(lbm::handle_pull_S(c->coarse, c->S), "pull coarse state");
-    lbm::drho_sum_kernel<<<256, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, c->part);
+    lbm::drho_sum_kernel<<<256, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, cbulk, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
-    lbm::correct_kernel<<<512, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, c->part, 256);
+    lbm::correct_kernel<<<512, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, cbulk, c->part, 256);
     CL_TRY(cudaGetLastError(), "correct");
     CL_TRY(lbm::handle_push_S(c->coarse, c->S), "push coarse state");
     return LBM_OK;
@@ -795,7 +823,7 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
 lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out) {
     if (!c || intervals < 0 || warmup_fine_steps < 0 || !coarse_out || !fine_out) return cl_fail(LBM_EINVAL, "invalid arguments");
-    if (use_net < 0 || use_net > 3) return cl_fail(LBM_EINVAL, "use_net must be 0, 1, 2 or 3");
+    if (use_net < 0 || use_net > 4) return cl_fail(LBM_EINVAL, "use_net must be 0 to 4");
     if (use_net && c->ntrain == 0) return cl_fail(LBM_ESTATE, "the network has not been trained");
     CL_STATUS(lbm::handle_reseed(c->fine, seed));
     CL_STATUS(lbm_step(c->fine, warmup_fine_steps));

@@ -18,7 +18,7 @@
 // (a thread takes 8 rows):
 //   D1 moments   : rho_A, rho_B, j (sum over components) per site; masses
 //   D2 velocity  : physical velocity u = (j + F/2) / rho; E_k, E_p, buoyancy,
-//                  row sums of phi, crossing counts
+//                  row sums of phi and of the mass fraction, crossing counts
 //   D3 tensors   : P^K, K^(tau), grad u + grad u^T per site; <u.grad p_b>, omega^2
 //   D4 divergence: <u . div P^K>, <u . div K^(tau)>, <u . div(grad u + grad u^T)>
 //   D5 reduce    : per-term and per-row sums of the block partials
@@ -95,7 +95,8 @@ struct DiagArgs {
     dfl* T;             // [9][ny][nx]
     double* F;          // [4][ny][nx] doubles (field extraction; aliases T)
     double* partials;   // [kDiagTerms][nblocks]
-    double* rowpart;    // [ny][nbx]
+    double* rowpart;    // [ny][nbx]: row partials of phi
+    double* rowpart_c;  // [ny][nbx]: row partials of the mass fraction rho_A / (rho_A + rho_B)
     int nblocks, nbx;   // blocks in total / along x
 };
 
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(DX * DY) velocity_kernel(DiagArgs a, int lo, i
         const int y = row_of(r);
         const bool valid = x < a.nx && y >= lo && y < hi && y < a.ny;
         const bool avg = valid && y >= a.r0 && y < a.r1;
-        dfl phi = {0.0f, 0.0f};
+        dfl phi = {0.0f, 0.0f}, cA = {0.0f, 0.0f};
         if (valid) {
             const size_t k = (size_t)y * a.nx + x;
             const dfl rA = a.M[k], rB = a.M[a.n + k], jx = a.M[2 * a.n + k], jy = a.M[3 * a.n + k];
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(DX * DY) velocity_kernel(DiagArgs a, int lo, i
                 a.F[3 * a.n + k] = to_d(uy);
             }
             phi = rA - rB;
+            if (rho.hi > 0.0f) cA = dfl_div(rA, rho);
             if (avg) {
                 v[0] = v[0] + rho * (ux * ux + uy * uy) * 0.5f;
                 v[1] = v[1] + phi * (float)y;
@@ -256,8 +258,11 @@ __global__ void __launch_bounds__(DX * DY) velocity_kernel(DiagArgs a, int lo, i
         if (accumulate) {   // uniform over the launch
             // row partial of phi: one warp is one row of 32 columns
             const dfl rs = warp_sum(avg ? phi : dfl{0.0f, 0.0f});
-            if (threadIdx.x == 0 && y < a.ny && y >= a.r0 && y < a.r1)
+            const dfl rc = warp_sum(avg ? cA : dfl{0.0f, 0.0f});
+            if (threadIdx.x == 0 && y < a.ny && y >= a.r0 && y < a.r1) {
                 a.rowpart[(size_t)y * a.nbx + blockIdx.x] = to_d(rs);
+                a.rowpart_c[(size_t)y * a.nbx + blockIdx.x] = to_d(rc);
+            }
         }
     }
     if (!accumulate) return;
@@ -362,7 +367,8 @@ __global__ void __launch_bounds__(DX * DY) divergence_kernel(DiagArgs a) {
     block_sums<3>(v, a, T_FLUX_K);
 }
 
-// blocks [0, kDiagTerms): term sums over the block partials; the next blocks: row sums.
+// blocks [0, kDiagTerms): term sums over the block partials; the next r1 - r0 blocks:
+// row sums of phi; the last r1 - r0 blocks: row sums of the mass fraction.
 __global__ void __launch_bounds__(256) reduce_kernel(DiagArgs a, double* out) {
     __shared__ double sm[256];
     const int tid = threadIdx.x;
@@ -371,8 +377,10 @@ __global__ void __launch_bounds__(256) reduce_kernel(DiagArgs a, double* out) {
         const double* p = a.partials + (size_t)blockIdx.x * a.nblocks;
         for (int b = tid; b < a.nblocks; b += 256) s += p[b];
     } else {
-        const int y = a.r0 + (blockIdx.x - kDiagTerms);
-        const double* p = a.rowpart + (size_t)y * a.nbx;
+        const int nrows = a.r1 - a.r0;
+        const int k = blockIdx.x - kDiagTerms;
+        const int y = a.r0 + (k < nrows ? k : k - nrows);
+        const double* p = (k < nrows ? a.rowpart : a.rowpart_c) + (size_t)y * a.nbx;
         for (int b = tid; b < a.nbx; b += 256) s += p[b];
     }
     sm[tid] = s;
@@ -414,6 +422,7 @@ DiagArgs make_args(const DiagLaunch& D) {
     a.nblocks = a.nbx * ((a.ny + BY - 1) / BY);
     a.partials = D.partials;
     a.rowpart = D.partials + (size_t)kDiagTerms * a.nblocks;
+    a.rowpart_c = a.rowpart + (size_t)a.ny * a.nbx;
     return a;
 }
 
@@ -438,7 +447,7 @@ size_t diag_scratch_doubles(int nx, int ny) { return (size_t)15 * nx * ny; }
 
 size_t diag_partials_doubles(int nx, int ny) {
     const size_t gx = (nx + DX - 1) / DX, gy = (ny + BY - 1) / BY;
-    return (size_t)kDiagTerms * gx * gy + (size_t)ny * gx;
+    return (size_t)kDiagTerms * gx * gy + (size_t)2 * ny * gx;
 }
 
 size_t diag_fields_offset(int nx, int ny) { return (size_t)6 * nx * ny; }
@@ -454,7 +463,7 @@ cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st) {
     velocity_kernel<<<grid, block, 0, st>>>(a, a.r0 - 2, a.r1 + 2, 1);
     tensor_kernel<<<grid, block, 0, st>>>(a);
     divergence_kernel<<<grid, block, 0, st>>>(a);
-    reduce_kernel<<<kDiagTerms + (a.r1 - a.r0), 256, 0, st>>>(a, D.out);
+    reduce_kernel<<<kDiagTerms + 2 * (a.r1 - a.r0), 256, 0, st>>>(a, D.out);
     return cudaGetLastError();
 }
 

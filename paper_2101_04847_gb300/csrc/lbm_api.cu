@@ -100,7 +100,7 @@ Layout make_layout(const lbm_params& p) {
                                        (size_t)18 * n * sizeof(double), L.pop_bytes});
     L.scratch = off; off = align_up(off + scratch_b);
     L.partials = off; off = align_up(off + lbm::diag_partials_doubles(p.nx, p.ny) * sizeof(double));
-    L.out = off; off = align_up(off + (lbm::kDiagTerms + (size_t)p.ny) * sizeof(double));
+    L.out = off; off = align_up(off + (lbm::kDiagTerms + 2 * (size_t)p.ny) * sizeof(double));
     L.flag = off; off = align_up(off + 16);
     L.y0 = off; off = align_up(off + (size_t)p.nx * sizeof(double));
     L.total = off;
@@ -148,7 +148,7 @@ struct lbm_handle {
     bool unstable = false;
     bool timed_out = false;
     bool in_ensemble = false;     // stepped by its ensemble only
-    double* host_out = nullptr;   // pinned, kDiagTerms + ny doubles
+    double* host_out = nullptr;   // pinned, kDiagTerms + 2 ny doubles
     std::vector<double> last_rows;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
@@ -507,7 +507,7 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
         }
         h->own_stream = true;
     }
-    cudaError_t e = cudaMallocHost((void**)&h->host_out, (lbm::kDiagTerms + (size_t)p->ny) * sizeof(double));
+    cudaError_t e = cudaMallocHost((void**)&h->host_out, (lbm::kDiagTerms + 2 * (size_t)p->ny) * sizeof(double));
     if (e != cudaSuccess) {
         h->host_out = nullptr;
         lbm_destroy(h);
@@ -624,7 +624,7 @@ lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
     lbm::DiagLaunch D = diag_launch(h);
     LBM_TRY(lbm::launch_diagnostics(D, h->stream), "diagnostics kernels");
     const int nrows = p.ny - 2 * p.crop_rows;
-    LBM_TRY(cudaMemcpyAsync(h->host_out, D.out, (lbm::kDiagTerms + (size_t)nrows) * sizeof(double),
+    LBM_TRY(cudaMemcpyAsync(h->host_out, D.out, (lbm::kDiagTerms + 2 * (size_t)nrows) * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream), "copy diagnostics");
     lbm_status st = check_flag(h);  // synchronises the stream
     if (st != LBM_OK && st != LBM_EUNSTABLE) return st;
@@ -649,15 +649,16 @@ lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
     for (int k = 0; k < 4; ++k) out->cc[k] = (int64_t)std::llround(o[lbm::T_N0 + k]);
     out->L_int = (M_PI / 8.0) * ((double)out->cc[0] + (double)out->cc[1] +
                                  ((double)out->cc[2] + (double)out->cc[3]) / std::sqrt(2.0));
-    // mixing-layer width from the normalised row means of phi
-    const double top = p.mass_A - p.minority * p.mass_B;
-    const double bot = p.minority * p.mass_A - p.mass_B;
+    // row means of phi (the profile) and the mixing-layer width from the normalised
+    // row means of the mass fraction rho_A / (rho_A + rho_B)
+    const double eps = p.minority;
+    const double top = p.mass_A / (p.mass_A + eps * p.mass_B);
+    const double bot = eps * p.mass_A / (eps * p.mass_A + p.mass_B);
     h->last_rows.assign(nrows, 0.0);
     double hw = 0.0;
     for (int r = 0; r < nrows; ++r) {
-        const double mean = o[lbm::kDiagTerms + r] / p.nx;
-        h->last_rows[r] = mean;
-        double c = (mean - bot) / (top - bot);
+        h->last_rows[r] = o[lbm::kDiagTerms + r] / p.nx;
+        double c = (o[lbm::kDiagTerms + nrows + r] / p.nx - bot) / (top - bot);
         c = c < 0.0 ? 0.0 : (c > 1.0 ? 1.0 : c);
         hw += c * (1.0 - c);
     }

@@ -152,8 +152,8 @@ struct DiagLaunch {
     double G, G_wall[2], g_ext[2], gx, tau_bar;
     int crop;
     double* scratch;     // 15 doubles per site
-    double* partials;    // kDiagTerms * nblocks + ny * nbx
-    double* out;         // kDiagTerms + ny doubles
+    double* partials;    // kDiagTerms * nblocks + 2 * ny * nbx
+    double* out;         // kDiagTerms + 2 * ny doubles (terms, row sums of phi, of the mass fraction)
 };
 size_t diag_scratch_doubles(int nx, int ny);
 size_t diag_partials_doubles(int nx, int ny);

@@ -384,7 +384,9 @@ class Closure:
 
     def evaluate(self, seed: int, warmup: int, intervals: int, use_net: int) -> tuple[list[dict], list[dict]]:
         """use_net: 0 no correction, 1 densities and velocity, 2 order parameter only,
-        3 order parameter and a quarter of the velocity correction."""
+        3 order parameter and a quarter of the velocity correction, 4 as 3 with the
+        order parameter corrected on the interface only (weight 4 c (1 - c) of the
+        normalised mass fraction)."""
         co = (LbmDiag * (intervals + 1))()
         fi = (LbmDiag * (intervals + 1))()
         _check(self.lib.lbm_closure_evaluate(self._c, seed, warmup, intervals, int(use_net), co, fi),

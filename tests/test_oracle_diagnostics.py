@@ -43,7 +43,7 @@ def test_cauchy_crofton_length_of_a_disk(R):
 
 # ---------------------------------------------------------------- mixing width
 def _width_of_profile(c, p):
-    top, bot = O.bulk_order_parameter(p)
+    top, bot = O.bulk_mass_fraction(p)
     return O.mixing_width(bot + c * (top - bot), p)
 
 
@@ -63,6 +63,23 @@ def test_mixing_width_of_a_linear_ramp():
     for w in (5, 40):
         c = np.concatenate([np.zeros(30), (np.arange(w) + 0.5) / w, np.ones(30)])
         assert abs(_width_of_profile(c, p) - (w + 0.5 / w)) < 1e-12 * w
+
+
+def test_mixing_width_ignores_a_compression_of_the_bulks():
+    # gravity compresses a tall column: both densities grow with depth by the same
+    # factor, which shifts the bulk rho_A - rho_B but not the mass fraction
+    p = fields_params(16, 400)
+    y = np.arange(400, dtype=float)[:, None] * np.ones((1, 16))
+    H = 0.5 * (1 + np.tanh((y - 200.3) / 3.0))
+    eps = p.minority
+    rhoA = p.mass_A * (eps + (1 - eps) * H)
+    rhoB = p.mass_B * (eps + (1 - eps) * (1 - H))
+    z = np.zeros_like(rhoA)
+    flat = O.field_diagnostics(rhoA, rhoB, z, z, p)["h"]
+    squeeze = 1.0 + 0.06 * (1.0 - y / 400.0)
+    pressed = O.field_diagnostics(rhoA * squeeze, rhoB * squeeze, z, z, p)["h"]
+    assert abs(pressed - flat) < 1e-9 * flat
+    assert abs(flat - 9.0) < 0.5          # about 3 half-widths of the tanh (W = 3)
 
 
 # ---------------------------------------------------------------- stress identities
