@@ -241,7 +241,8 @@ void lbm_ens_destroy(lbm_ensemble* e);
 /* ---- Learned closure of a 2x-coarsened run (an extension built on the solver;
  * the paper has none).  CNN: conv3x3 4->32, ReLU, conv3x3 32->32, ReLU,
  * conv3x3 32->4 on fields [4][ny][nx] = (rho_A, rho_B, u_x, u_y), x periodic and
- * zero padding beyond the walls; BF16 weights, FP32 activations and accumulation.
+ * zero padding beyond the walls; BF16 weights, FP32 accumulation; FP32 activations in
+ * lbm_cnn_forward and the training kernels, BF16 activations in lbm_cnn_infer.
  * Parameters: one FP32 vector of LBM_CNN_PARAMS values, w1[32][4][3][3], b1[32],
  * w2[32][32][3][3], b2[32], w3[4][32][3][3], b3[4]. ---- */
 #define LBM_CNN_PARAMS 11588
@@ -252,6 +253,18 @@ lbm_status lbm_cnn_workspace_bytes(int32_t nx, int32_t ny, size_t* bytes);
 /* y = CNN(x); all pointers device (x, y: 4*ny*nx floats). Asynchronous. */
 lbm_status lbm_cnn_forward(const float* params, const float* x, int32_t nx, int32_t ny, void* workspace,
                            size_t ws_bytes, void* cuda_stream, float* y);
+
+/* y = CNN(x) on the tensor cores (tcgen05): x and both hidden layers rounded to
+ * BF16 (nearest even), FP32 accumulation; same parameters, layouts and workspace
+ * as lbm_cnn_forward.  The learned closure corrects with this path.
+ * Asynchronous; a bounded wait inside the kernels that gave up is reported by
+ * lbm_cnn_infer_status. */
+lbm_status lbm_cnn_infer(const float* params, const float* x, int32_t nx, int32_t ny, void* workspace,
+                         size_t ws_bytes, void* cuda_stream, float* y);
+
+/* Synchronises the stream; LBM_ETIMEOUT if a wait of the last lbm_cnn_infer on
+ * this workspace gave up (its output is then incomplete), else LBM_OK. */
+lbm_status lbm_cnn_infer_status(void* workspace, int32_t nx, int32_t ny, void* cuda_stream);
 
 /* loss = mean((CNN(x) - t)^2) over the 4*ny*nx outputs (host), grad = dloss/dparams
  * (device, LBM_CNN_PARAMS floats).  Synchronises the stream. */

@@ -55,6 +55,25 @@ def forward(params: np.ndarray, x: np.ndarray) -> dict:
     return dict(x=x, z1=z1, a1=a1, z2=z2, a2=a2, y=y)
 
 
+def round_bf16(a: torch.Tensor) -> torch.Tensor:
+    """Round to FP32 and then to BFloat16 (8 significant bits), both to nearest
+    even, returned in float64: the storage format of 16-bit activations."""
+    b = a.to(torch.float32).numpy().view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return torch.tensor(b.astype(np.uint32).view(np.float32).astype(np.float64))
+
+
+def forward_bf16_activations(params: np.ndarray, x: np.ndarray) -> dict:
+    """The network as evaluated with BF16 activations: the input and both hidden
+    layers (after ReLU) are rounded to BF16 before the next convolution, all
+    arithmetic in float64."""
+    w1, b1, w2, b2, w3, b3 = unpack(params)
+    x = round_bf16(torch.tensor(np.asarray(x, dtype=np.float64)))
+    a1 = round_bf16(torch.relu(conv(x, w1, b1)))
+    a2 = round_bf16(torch.relu(conv(a1, w2, b2)))
+    return dict(x=x, a1=a1, a2=a2, y=conv(a2, w3, b3))
+
+
 def loss(params: np.ndarray, x: np.ndarray, t: np.ndarray) -> float:
     y = forward(params, x)["y"]
     return float(torch.mean((y - torch.tensor(np.asarray(t, dtype=np.float64))) ** 2))

@@ -13,6 +13,7 @@
 // (tau_c = 1/2 + (tau - 1/2)/2) would move the coarse mixture deeper into the
 // immiscible regime and drive its minority densities negative.
 #include "lattice.cuh"
+#include "cnn_tc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -229,11 +230,13 @@ struct Net {
     float *a1, *a2, *y, *dy, *dz2, *dz1, *part;
     double* lpart;
     int P;
+    cnn_tc::Bufs tc;   // tensor-core inference
 };
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-size_t workspace_bytes(int nx, int ny) {
+// FP32 forward/backward buffers, then the tensor-core inference planes
+size_t training_bytes(int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     const size_t P = (n + kChunk - 1) / kChunk;
     size_t b = align256(kParams * sizeof(__nv_bfloat16));
@@ -242,6 +245,8 @@ size_t workspace_bytes(int nx, int ny) {
     b += align256(1024 * sizeof(double));
     return b;
 }
+
+size_t workspace_bytes(int nx, int ny) { return training_bytes(nx, ny) + cnn_tc::bytes(nx, ny); }
 
 Net carve(void* ws, int nx, int ny) {
     Net N;
@@ -259,6 +264,7 @@ Net carve(void* ws, int nx, int ny) {
     N.dz1 = (float*)p; p += align256(kHid * N.n * 4);
     N.part = (float*)p; p += align256((size_t)N.P * kHid * kHid * 10 * 4);
     N.lpart = (double*)p;
+    N.tc = cnn_tc::carve((char*)ws + training_bytes(nx, ny), nx, ny);
     return N;
 }
 
@@ -579,7 +585,7 @@ lbm_status correct(lbm_closure* c, int mode) {
     lbm::normalize_kernel<<<512, 256, 0, c->stream>>>(c->raw, nullptr, c->nc, f4(c->in_mean), f4(c->in_scale),
                                                       f4(c->out_scale), c->xin, nullptr);
     CL_TRY(cudaGetLastError(), "normalize");
-    CL_TRY(lbm::cnn::forward(c->net, c->params, c->xin, c->yout, c->stream), "cnn forward");
+    CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
     CL_TRY(lbm::handle_pull_S(c->coarse, c->S), "pull coarse state");
     lbm::drho_sum_kernel<<<256, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, cbulk, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
@@ -605,6 +611,24 @@ lbm_status lbm_cnn_forward(const float* params, const float* x, int32_t nx, int3
     if (ws_bytes < lbm::cnn::workspace_bytes(nx, ny)) return cl_fail(LBM_ENOMEM, "CNN workspace too small");
     lbm::cnn::Net N = lbm::cnn::carve(ws, nx, ny);
     CL_TRY(lbm::cnn::forward(N, params, x, y, (cudaStream_t)stream), "cnn forward");
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_infer(const float* params, const float* x, int32_t nx, int32_t ny, void* ws, size_t ws_bytes,
+                         void* stream, float* y) {
+    if (!params || !x || !ws || !y || nx < 1 || ny < 1) return cl_fail(LBM_EINVAL, "NULL argument or empty grid");
+    if (ws_bytes < lbm::cnn::workspace_bytes(nx, ny)) return cl_fail(LBM_ENOMEM, "CNN workspace too small");
+    lbm::cnn::Net N = lbm::cnn::carve(ws, nx, ny);
+    CL_TRY(lbm::cnn_tc::infer(N.tc, params, x, y, (cudaStream_t)stream), "cnn inference");
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_infer_status(void* ws, int32_t nx, int32_t ny, void* stream) {
+    if (!ws || nx < 1 || ny < 1) return cl_fail(LBM_EINVAL, "NULL workspace or empty grid");
+    lbm::cnn::Net N = lbm::cnn::carve(ws, nx, ny);
+    int st = 0;
+    CL_TRY(lbm::cnn_tc::status(N.tc, (cudaStream_t)stream, &st), "cnn inference status");
+    if (st != 0) return cl_fail(LBM_ETIMEOUT, "a wait of the tensor-core CNN kernels gave up (status " + std::to_string(st) + ")");
     return LBM_OK;
 }
 
@@ -838,6 +862,11 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
         lbm_status st = lbm_diagnostics(c->coarse, &coarse_out[k]);
         if (st != LBM_OK) return st;   // the caller falls back to the fine run (fine_out stays valid)
         CL_STATUS(lbm_diagnostics(c->fine, &fine_out[k]));
+    }
+    if (use_net) {
+        int st = 0;
+        CL_TRY(lbm::cnn_tc::status(c->net.tc, c->stream, &st), "cnn inference status");
+        if (st != 0) return cl_fail(LBM_ETIMEOUT, "a wait of the tensor-core CNN kernels gave up");
     }
     return LBM_OK;
 }

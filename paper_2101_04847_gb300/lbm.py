@@ -82,6 +82,9 @@ _PROTOS = {
     "lbm_cnn_workspace_bytes": (C.c_int, [C.c_int32, C.c_int32, _P(C.c_size_t)]),
     "lbm_cnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
                                   C.c_void_p, C.c_void_p]),
+    "lbm_cnn_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
+                                C.c_void_p, C.c_void_p]),
+    "lbm_cnn_infer_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "lbm_cnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                     C.c_size_t, C.c_void_p, _P(C.c_double), C.c_void_p]),
     "lbm_closure_coarse_params": (C.c_int, [_P(LbmParams), _P(LbmParams)]),
@@ -356,6 +359,47 @@ class Ensemble:
 
 
 CNN_PARAMS = 11588
+
+
+class Cnn:
+    """The closure CNN on device tensors of one image size: `forward` (FP32
+    activations, the training path) and `infer` (tensor cores, BF16 activations).
+    Arguments are torch CUDA tensors: params [CNN_PARAMS] float32, x and y
+    [4, ny, nx] float32.  Calls are asynchronous on `stream` (default: the
+    current torch stream); `status()` synchronises and raises if a bounded wait
+    inside the inference kernels gave up."""
+
+    def __init__(self, nx: int, ny: int, stream=None):
+        import torch
+
+        self.lib = load_library()
+        self.nx, self.ny = int(nx), int(ny)
+        n = C.c_size_t()
+        _check(self.lib.lbm_cnn_workspace_bytes(self.nx, self.ny, C.byref(n)), "lbm_cnn_workspace_bytes")
+        self.ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self._stream = stream
+
+    def _st(self):
+        import torch
+
+        s = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def _args(self, params, x, y):
+        for t in (params, x, y):
+            assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()
+        return (C.c_void_p(params.data_ptr()), C.c_void_p(x.data_ptr()), self.nx, self.ny,
+                C.c_void_p(self.ws.data_ptr()), self.ws.numel(), self._st(), C.c_void_p(y.data_ptr()))
+
+    def forward(self, params, x, y):
+        _check(self.lib.lbm_cnn_forward(*self._args(params, x, y)), "lbm_cnn_forward")
+
+    def infer(self, params, x, y):
+        _check(self.lib.lbm_cnn_infer(*self._args(params, x, y)), "lbm_cnn_infer")
+
+    def status(self):
+        _check(self.lib.lbm_cnn_infer_status(C.c_void_p(self.ws.data_ptr()), self.nx, self.ny, self._st()),
+               "lbm_cnn_infer_status")
 
 
 class Closure:

@@ -43,3 +43,42 @@ def test_gradient_matches_central_differences():
         e[i] = h
         fd = (N.loss(p + e, x, t) - N.loss(p - e, x, t)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) * max(abs(L), 1e-3), (i, fd, g[i])
+
+
+def test_bf16_activation_forward_against_the_exact_network():
+    # the BF16-activation network stays within the worst-case rounding bound of the
+    # exact one, differs from it (the roundings happen), and a plausible mistake in
+    # the middle layer (a dropped tap, transposed channels) moves most outputs by far
+    # more than the 1e-5 the GPU comparison allows off the rounding-flip cases
+    from tests.cnn_bound import bf16_activation_bound
+
+    rng = np.random.default_rng(3)
+    p = N.init_params(4)
+    p[1152:1184] = rng.normal(0, 0.1, 32)
+    for off, n in ((0, 1152), (1184, 9216), (10432, 1152)):
+        p[off:off + n] = N.round_bf16(torch.tensor(p[off:off + n])).numpy()
+    x = rng.normal(size=(4, 12, 20))
+    ref, bound = bf16_activation_bound(p, x)
+    emu = N.forward_bf16_activations(p, x)
+    y = emu["y"].numpy()
+    assert np.all(np.abs(y - ref) <= bound)
+    assert np.max(np.abs(y - ref)) > 1e-3 * np.max(np.abs(ref))
+    # rounding is idempotent: the stored activations are BF16 values
+    assert torch.equal(N.round_bf16(emu["a1"]), emu["a1"])
+    for mistake in ("dropped tap", "transposed"):
+        q = p.copy()
+        w = q[1184:1184 + 9216].reshape(32, 32, 3, 3)
+        if mistake == "dropped tap":
+            w[:, :, 0, 2] = 0.0
+        else:
+            w[:] = w.transpose(1, 0, 2, 3).copy()
+        bad = N.forward_bf16_activations(q, x)["y"].numpy()
+        assert np.mean(np.abs(bad - y) > 1e-5 * np.max(np.abs(y))) > 0.5, mistake
+
+
+def test_round_bf16_against_hand_values():
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: to even (1); 1 + 3 * 2^-8 rounds up
+    # to 1 + 2^-6 (even); 2^-7 spacing at 1; values already BF16 stay
+    v = torch.tensor([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -3.0, 0.0, 1.5 + 2.0 ** -7])
+    want = [1.0, 1.0, 1.0 + 2.0 ** -6, 1.0, -3.0, 0.0, 1.5 + 2.0 ** -7]
+    assert N.round_bf16(v).tolist() == want
