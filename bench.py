@@ -478,6 +478,87 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_closure(args):
+    """Throughput of the learned closure at the fine workload's size: the 2x-coarsened
+    run (nx/2 x ny/2, one coarse step = four fine steps) advanced in intervals of 10
+    coarse steps, corrected after each (interface order parameter + velocity / 4),
+    against the plain FP32 fine solver covering the same physical time.  The network
+    has untrained He-scaled weights (the kernels' cost does not depend on them); its
+    accuracy is measured on the 128x256 workload by the closure tests."""
+    import numpy as np
+    import torch
+
+    from paper_2101_04847_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    interval, mode = 10, 4
+    fine = lbm.default_params(**workload(args), seed=1)
+    stream = torch.cuda.Stream()
+    c = lbm.Closure(fine, interval=interval, seed=0, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    parts = []
+    for shape in ((32, 4, 3, 3), (32,), (32, 32, 3, 3), (32,), (4, 32, 3, 3), (4,)):
+        if len(shape) == 4:
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / (shape[1] * 9)), size=shape).ravel() * (0.1 if shape[0] == 4 else 1.0))
+        else:
+            parts.append(np.zeros(shape))
+    c.set_params(np.concatenate(parts).astype(np.float32))
+    f_solver, c_solver = c.solvers()
+    ncx, ncy = c.coarse.nx, c.coarse.ny
+    cnn = lbm.Cnn(ncx, ncy, stream=stream)
+    dp = torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda()
+    dx = torch.randn(4, ncy, ncx, device="cuda")
+    dy = torch.empty_like(dx)
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    for _ in range(args.warmup):
+        c.advance(1, mode)
+        c.advance(1, 0)
+        cnn.infer(dp, dx, dy)
+    f_solver.step(4 * interval)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        corrected = timed(lambda: c.advance(1, mode), args.steps)
+        coarse = timed(lambda: c.advance(1, 0), args.steps)
+        infer = timed(lambda: cnn.infer(dp, dx, dy), args.steps)
+        plain = timed(lambda: f_solver.step(4 * interval), max(1, args.steps // 2))
+    cnn.status()
+    fine_sites = fine.nx * fine.ny
+    fine_equiv = fine_sites * 4 * interval
+    out = {
+        "kind": "closure",
+        "metric": "fine-equivalent MLUPS (fine sites x fine steps covered per second)",
+        "unit": "MLUPS",
+        "value": fine_equiv / (corrected * 1e-3) / 1e6,
+        "higher_is_better": True,
+        "dtype": "f32 populations, bf16 CNN activations",
+        "data": "synthetic",
+        "config": {"workload": f"fine {fine.nx}x{fine.ny} / coarse {ncx}x{ncy} two-component D2Q9 Shan-Chen "
+                               f"Rayleigh-Taylor, G=1.4, interval {interval} coarse steps, correction mode {mode}",
+                   "weights": "untrained (He-scaled); throughput only"},
+        "ms_per_interval": {"coarse_steps": coarse, "coarse_steps_and_correction": corrected,
+                            "correction": corrected - coarse, "cnn_inference": infer,
+                            "plain_fine_steps": plain},
+        "plain_fine_MLUPS": fine_equiv / (plain * 1e-3) / 1e6,
+        "speedup_vs_plain_fine": plain / corrected,
+        "steps": args.steps, "warmup": args.warmup,
+        "accuracy": "measured on 128x256 fine / 64x128 coarse (tests/test_gpu_closure.py), not at this size",
+        "clocks": clocks.summary(),
+    }
+    c.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +575,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
     ap.add_argument("--ensemble-grid", dest="ensemble_grid", default="",
                     help="with --ensemble: put every member on this NXxNY grid instead of the drawn ones")
+    ap.add_argument("--closure", action="store_true",
+                    help="time the learned closure (coarse run + correction) against the plain fine solver")
     ap.add_argument("--storage-study", dest="storage_study", type=int, default=0,
                     help="advance FP32, FP16 and BF16 storage this many LB steps and compare their diagnostics")
     args = ap.parse_args()
@@ -505,6 +588,8 @@ def main():
         run_ensemble(args)
     elif args.storage_study:
         run_storage_study(args)
+    elif args.closure:
+        run_closure(args)
     else:
         run_ours(args)
 

@@ -306,6 +306,13 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
 lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out);
 
+/* Production use of the closure: advance the coarse run by `intervals` intervals
+ * of `interval` coarse steps, correcting it after each with mode use_net (0 = no
+ * correction, 1-4 as in lbm_closure_evaluate), without running the fine solver.
+ * Needs trained (or set) parameters for use_net > 0 (else LBM_ESTATE).
+ * Asynchronous on the closure's stream except where a correction reads back. */
+lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_net);
+
 /* Copy the network parameters to (set = 0) or from (set = 1) host memory. */
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set);
 

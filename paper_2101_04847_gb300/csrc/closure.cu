@@ -375,43 +375,51 @@ __global__ void normalize_kernel(const float* __restrict__ raw, const float* __r
 // mode 1: drho_A and drho_B as predicted; modes 2 and 3: only the order parameter,
 // drho_A = -drho_B = (drho_A - drho_B) / 2, so the total density is unchanged;
 // mode 4: the order parameter times the interface weight w (below).
-__device__ __forceinline__ void limited_drho(int mode, const double rho[2], double pA, double pB, double w,
-                                             double d[2]) {
+__device__ __forceinline__ void limited_drho(int mode, const float rho[2], float pA, float pB, float w, float d[2]) {
     if (mode >= 2) {
-        const double s = mode == 4 ? w : 1.0;
-        const double h = fmin(fmax(0.5 * s * (pA - pB), -0.5 * rho[0]), 0.5 * rho[1]);
+        const float s = mode == 4 ? w : 1.0f;
+        const float h = fminf(fmaxf(0.5f * s * (pA - pB), -0.5f * rho[0]), 0.5f * rho[1]);
         d[0] = h;
         d[1] = -h;
     } else {
-        d[0] = fmax(pA, -0.5 * rho[0]);
-        d[1] = fmax(pB, -0.5 * rho[1]);
+        d[0] = fmaxf(pA, -0.5f * rho[0]);
+        d[1] = fmaxf(pB, -0.5f * rho[1]);
     }
 }
 
 // Interface weight w = 4 c (1 - c) of the normalised mass fraction
 // c = (rho_A / rho - c_bot) / (c_top - c_bot), clamped to [0, 1]: 1 on the interface,
 // 0 in either bulk, so that mode 4 leaves the bulk composition alone.
-__device__ __forceinline__ double interface_weight(const double rho[2], double2 cbulk) {
-    const double r = rho[0] + rho[1];
-    if (!(r > 0.0)) return 0.0;
-    const double c = fmin(fmax((rho[0] / r - cbulk.y) / (cbulk.x - cbulk.y), 0.0), 1.0);
-    return 4.0 * c * (1.0 - c);
+__device__ __forceinline__ float interface_weight(const float rho[2], float2 cbulk) {
+    const float r = rho[0] + rho[1];
+    if (!(r > 0.0f)) return 0.0f;
+    const float c = fminf(fmaxf((rho[0] / r - cbulk.y) / (cbulk.x - cbulk.y), 0.0f), 1.0f);
+    return 4.0f * c * (1.0f - c);
 }
 
-// sums of the limited density corrections (per block partials, fixed order); the
-// densities come from the populations S of the coarse run
-// (mode 4: the sum of the order-parameter corrections and the sum of the weights)
-__global__ void drho_sum_kernel(const double* __restrict__ S, const float* __restrict__ y, size_t n, float4 oscale,
-                                int mode, double2 cbulk, double* __restrict__ part) {
+__device__ __forceinline__ void site_densities(const float* __restrict__ S, size_t n, size_t k, float rho[2]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float r = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r += S[(size_t)(s * 9 + i) * n + k];
+        rho[s] = r;
+    }
+}
+
+// Per-block sums (FP64) of the limited density corrections, from the populations S
+// of the coarse run (FP32, [18][n]); mode 4: the sum of the order-parameter
+// corrections and the sum of the weights.
+__global__ void __launch_bounds__(256) drho_sum_kernel(const float* __restrict__ S, const float* __restrict__ y, size_t n,
+                                                       float4 oscale, int mode, float2 cbulk, double* __restrict__ part) {
     __shared__ double red[2][8];
     double a = 0.0, b = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        double rho[2] = {0.0, 0.0};
-        for (int s = 0; s < 2; ++s)
-            for (int i = 0; i < 9; ++i) rho[s] += S[(size_t)(s * 9 + i) * n + k];
-        const double w = interface_weight(rho, cbulk);
-        double d[2];
-        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, w, d);
+        float rho[2];
+        site_densities(S, n, k, rho);
+        const float w = interface_weight(rho, cbulk);
+        float d[2];
+        limited_drho(mode, rho, y[k] * oscale.x, y[n + k] * oscale.y, w, d);
         a += d[0];
         b += mode == 4 ? w : d[1];
     }
@@ -428,38 +436,52 @@ __global__ void drho_sum_kernel(const double* __restrict__ S, const float* __res
     }
 }
 
+// The block partials summed in a fixed order into part[2 nparts], part[2 nparts + 1].
+__global__ void drho_total_kernel(double* __restrict__ part, int nparts) {
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int p = 0; p < nparts; ++p) v += part[2 * p + threadIdx.x];
+        part[2 * nparts + threadIdx.x] = v;
+    }
+}
+
 // Re-equilibration with the corrected moments: with rho'_s = rho_s + drho_s - mean
 // (drho limited as above, the mean over the grid removed so that each component's
 // mass is unchanged; mode 4 removes it in proportion to the interface weight,
 // drho_A = -drho_B = h - w sum(h) / sum(w)) and u' = u_b + du in mode 1, u_b in
 // mode 2 and u_b + du / 4 in modes 3 and 4 (u_b = j / rho of S itself),
 //   f <- f^eq(rho'_s, u') + (rho'_s / rho_s) (f - f^eq(rho_s, u_b)),
-// i.e. the non-equilibrium part is kept in proportion to the density.
-__global__ void correct_kernel(double* __restrict__ S, const float* __restrict__ y, size_t n, float4 oscale,
-                               int mode, double2 cbulk, const double* __restrict__ part, int nparts) {
-    double mA = 0.0, mB = 0.0;
-    for (int p = 0; p < nparts; ++p) { mA += part[2 * p]; mB += part[2 * p + 1]; }
-    const double hw = mode == 4 && mB > 0.0 ? mA / mB : 0.0;   // mode 4: sum(h) / sum(w)
-    mA /= (double)n;
-    mB /= (double)n;
+// i.e. the non-equilibrium part is kept in proportion to the density.  FP32 per
+// site: the corrections are small next to the populations, and the mass sums are
+// FP64.
+__global__ void __launch_bounds__(256) correct_kernel(float* __restrict__ S, const float* __restrict__ y, size_t n,
+                                                      float4 oscale, int mode, float2 cbulk,
+                                                      const double* __restrict__ total) {
+    const double sA = total[0], sB = total[1];
+    const float hw = mode == 4 && sB > 0.0 ? (float)(sA / sB) : 0.0f;   // mode 4: sum(h) / sum(w)
+    const float mA = (float)(sA / (double)n), mB = (float)(sB / (double)n);
+    // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
+    // full correction of mode 1 feeds back into the growing coarse modes)
+    const float du = mode == 1 ? 1.0f : (mode >= 3 ? 0.25f : 0.0f);
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        double rho[2] = {0, 0}, jx = 0, jy = 0;
+        float f[2][9];
+        float rho[2] = {0.0f, 0.0f}, jx = 0.0f, jy = 0.0f;
+#pragma unroll
         for (int s = 0; s < 2; ++s)
+#pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const double f = S[(size_t)(s * 9 + i) * n + k];
-                rho[s] += f;
-                jx += cx(i) * f;
-                jy += cy(i) * f;
+                f[s][i] = S[(size_t)(s * 9 + i) * n + k];
+                rho[s] += f[s][i];
+                jx += cx(i) * f[s][i];
+                jy += cy(i) * f[s][i];
             }
-        const double r = rho[0] + rho[1];
-        const double ux = jx / r, uy = jy / r;
-        // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
-        // full correction of mode 1 feeds back into the growing coarse modes)
-        const double du = mode == 1 ? 1.0 : (mode >= 3 ? 0.25 : 0.0);
-        const double vx = ux + du * (double)y[2 * n + k] * oscale.z, vy = uy + du * (double)y[3 * n + k] * oscale.w;
-        const double w = interface_weight(rho, cbulk);
-        double d[2];
-        limited_drho(mode, rho, (double)y[k] * oscale.x, (double)y[n + k] * oscale.y, w, d);
+        const float r = rho[0] + rho[1];
+        if (!(r > 0.0f)) continue;
+        const float ux = jx / r, uy = jy / r;
+        const float vx = ux + du * y[2 * n + k] * oscale.z, vy = uy + du * y[3 * n + k] * oscale.w;
+        const float w = interface_weight(rho, cbulk);
+        float d[2];
+        limited_drho(mode, rho, y[k] * oscale.x, y[n + k] * oscale.y, w, d);
         if (mode == 4) {
             d[0] -= w * hw;
             d[1] = -d[0];
@@ -467,17 +489,19 @@ __global__ void correct_kernel(double* __restrict__ S, const float* __restrict__
             d[0] -= mA;
             d[1] -= mB;
         }
+        const float u2 = ux * ux + uy * uy, v2 = vx * vx + vy * vy;
+#pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const double r0 = rho[s];
-            if (!(r0 > 0.0)) continue;
-            const double r1 = fmax(r0 + d[s], 0.0);
-            const double q = r1 / r0;
+            const float r0 = rho[s];
+            if (!(r0 > 0.0f)) continue;
+            const float r1 = fmaxf(r0 + d[s], 0.0f);
+            const float q = r1 / r0;
+#pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const double c0 = cx(i) * ux + cy(i) * uy, c1 = cx(i) * vx + cy(i) * vy;
-                const double e0 = wd(i) * r0 * (1.0 + 3.0 * c0 + 4.5 * c0 * c0 - 1.5 * (ux * ux + uy * uy));
-                const double e1 = wd(i) * r1 * (1.0 + 3.0 * c1 + 4.5 * c1 * c1 - 1.5 * (vx * vx + vy * vy));
-                double& f = S[(size_t)(s * 9 + i) * n + k];
-                f = e1 + q * (f - e0);
+                const float c0 = cx(i) * ux + cy(i) * uy, c1 = cx(i) * vx + cy(i) * vy;
+                const float e0 = wf(i) * r0 * (1.0f + 3.0f * c0 + 4.5f * c0 * c0 - 1.5f * u2);
+                const float e1 = wf(i) * r1 * (1.0f + 3.0f * c1 + 4.5f * c1 * c1 - 1.5f * v2);
+                S[(size_t)(s * 9 + i) * n + k] = e1 + q * (f[s][i] - e0);
             }
         }
     }
@@ -540,12 +564,18 @@ struct lbm_closure {
     std::vector<float*> samp_raw, samp_tgt;                    // raw coarse / restricted fine after an interval
     float *train_x = nullptr, *train_t = nullptr;
     int ntrain = 0;
+    bool have_params = false;                                  // trained or set by the caller
     float in_mean[4] = {0, 0, 0, 0}, in_scale[4] = {1, 1, 1, 1}, out_scale[4] = {1, 1, 1, 1};
 };
 
 namespace {
 
 float4 f4(const float* a) { return make_float4(a[0], a[1], a[2], a[3]); }
+
+// blocks of the correction's mass sums: 2 partials each + 2 totals fit the
+// 1024-double partial buffer
+constexpr int kCorrBlocks = 480;
+static_assert(2 * kCorrBlocks + 2 <= 1024, "correction partials");
 
 // restricted fields of the fine run into c->raw (or `dst`)
 lbm_status restrict_fine(lbm_closure* c, float* dst) {
@@ -586,12 +616,17 @@ lbm_status correct(lbm_closure* c, int mode) {
                                                       f4(c->out_scale), c->xin, nullptr);
     CL_TRY(cudaGetLastError(), "normalize");
     CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
-    CL_TRY(lbm::handle_pull_S(c->coarse, c->S), "pull coarse state");
-    lbm::drho_sum_kernel<<<256, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, cbulk, c->part);
+    // the FP32 copy of the coarse populations lives in the FP64 state buffer
+    float* Sf = reinterpret_cast<float*>(c->S);
+    CL_TRY(lbm::handle_pull_Sf(c->coarse, Sf), "pull coarse state");
+    const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
+    lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
-    lbm::correct_kernel<<<512, 256, 0, c->stream>>>(c->S, c->yout, c->nc, f4(c->out_scale), mode, cbulk, c->part, 256);
+    lbm::drho_total_kernel<<<1, 32, 0, c->stream>>>(c->part, kCorrBlocks);
+    lbm::correct_kernel<<<kCorrBlocks * 4, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,
+                                                                c->part + 2 * kCorrBlocks);
     CL_TRY(cudaGetLastError(), "correct");
-    CL_TRY(lbm::handle_push_S(c->coarse, c->S), "push coarse state");
+    CL_TRY(lbm::handle_push_Sf(c->coarse, Sf), "push coarse state");
     return LBM_OK;
 }
 
@@ -840,6 +875,7 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
         }
         last = sum / ((double)ns * 4 * n);
     }
+    c->have_params = true;
     if (final_loss) *final_loss = last;
     return LBM_OK;
 }
@@ -848,7 +884,7 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out) {
     if (!c || intervals < 0 || warmup_fine_steps < 0 || !coarse_out || !fine_out) return cl_fail(LBM_EINVAL, "invalid arguments");
     if (use_net < 0 || use_net > 4) return cl_fail(LBM_EINVAL, "use_net must be 0 to 4");
-    if (use_net && c->ntrain == 0) return cl_fail(LBM_ESTATE, "the network has not been trained");
+    if (use_net && !c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
     CL_STATUS(lbm::handle_reseed(c->fine, seed));
     CL_STATUS(lbm_step(c->fine, warmup_fine_steps));
     CL_STATUS(restrict_fine(c, c->raw));
@@ -871,12 +907,24 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
     return LBM_OK;
 }
 
+lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_net) {
+    if (!c || intervals < 0) return cl_fail(LBM_EINVAL, "invalid arguments");
+    if (use_net < 0 || use_net > 4) return cl_fail(LBM_EINVAL, "use_net must be 0 to 4");
+    if (use_net && !c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
+    for (int k = 0; k < intervals; ++k) {
+        CL_STATUS(lbm_step(c->coarse, c->interval));
+        if (use_net) CL_STATUS(correct(c, use_net));
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set) {
     if (!c || !host) return cl_fail(LBM_EINVAL, "NULL argument");
     const size_t bytes = lbm::cnn::kParams * 4;
-    if (set)
+    if (set) {
         CL_TRY(cudaMemcpy(c->params, host, bytes, cudaMemcpyHostToDevice), "set parameters");
-    else
+        c->have_params = true;
+    } else
         CL_TRY(cudaMemcpy(host, c->params, bytes, cudaMemcpyDeviceToHost), "get parameters");
     return LBM_OK;
 }

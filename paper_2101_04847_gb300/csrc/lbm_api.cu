@@ -320,6 +320,12 @@ cudaError_t handle_pull_S(lbm_handle* h, double* S) {
 cudaError_t handle_push_S(lbm_handle* h, const double* S) {
     return launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }
+cudaError_t handle_pull_Sf(lbm_handle* h, float* S) {
+    return launch_pull_to_float(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream);
+}
+cudaError_t handle_push_Sf(lbm_handle* h, const float* S) {
+    return launch_push_from_float(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
+}
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed) {
     h->p.seed = seed;
     destroy_graphs(h);

@@ -116,6 +116,8 @@ cudaError_t handle_restore_state(lbm_handle* h);
 cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy);
 cudaError_t handle_pull_S(lbm_handle* h, double* S);
 cudaError_t handle_push_S(lbm_handle* h, const double* S);
+cudaError_t handle_pull_Sf(lbm_handle* h, float* S);         // as handle_pull_S, FP32 copy
+cudaError_t handle_push_Sf(lbm_handle* h, const float* S);
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed);
 
 // message returned by lbm_last_error() on this thread (lbm_api.cu)

@@ -91,6 +91,7 @@ _PROTOS = {
     "lbm_closure_create": (C.c_int, [_P(LbmParams), C.c_int32, C.c_uint64, C.c_void_p, _P(C.c_void_p)]),
     "lbm_closure_generate": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_int32, C.c_int32]),
     "lbm_closure_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_uint64, _P(C.c_double)]),
+    "lbm_closure_advance": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "lbm_closure_evaluate": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, _P(LbmDiag),
                                        _P(LbmDiag)]),
     "lbm_closure_params": (C.c_int, [C.c_void_p, _P(C.c_float), C.c_int32]),
@@ -436,6 +437,10 @@ class Closure:
         _check(self.lib.lbm_closure_evaluate(self._c, seed, warmup, intervals, int(use_net), co, fi),
                "lbm_closure_evaluate")
         return [diag_dict(d) for d in co], [diag_dict(d) for d in fi]
+
+    def advance(self, intervals: int, use_net: int):
+        """Advance the coarse run by `intervals` corrected intervals (no fine run)."""
+        _check(self.lib.lbm_closure_advance(self._c, int(intervals), int(use_net)), "lbm_closure_advance")
 
     def params(self) -> np.ndarray:
         out = np.empty(CNN_PARAMS, dtype=np.float32)

@@ -142,3 +142,25 @@ def test_closure_against_the_coarse_run_without_it(gpu, trained):
             assert all(abs(d[s] - co[0][s]) <= 1e-5 * co[0][s] for d in co)   # corrections keep the masses
     with pytest.raises(lbm.LbmError):
         c.evaluate(seed=101, warmup=0, intervals=1, use_net=5)
+
+
+def test_advance_runs_the_corrected_coarse_solver_alone(gpu, trained):
+    # production use: the coarse run advanced in corrected intervals, no fine run
+    c, _ = trained
+    _, co = c.solvers()
+    m0 = co.diagnostics()
+    n0 = co.step_count
+    c.advance(3, 4)
+    m1 = co.diagnostics()
+    assert co.step_count == n0 + 3 * 10, (n0, co.step_count)
+    for s in ("mass_A", "mass_B"):
+        assert abs(m1[s] - m0[s]) <= 1e-5 * m0[s], (s, m0[s], m1[s])
+    c.advance(2, 0)
+    assert co.step_count == n0 + 5 * 10
+    fresh = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    with pytest.raises(lbm.LbmError):
+        fresh.advance(1, 4)                      # no trained or set parameters
+    fresh.advance(1, 0)
+    with pytest.raises(lbm.LbmError):
+        fresh.advance(1, 5)
+    fresh.close()
