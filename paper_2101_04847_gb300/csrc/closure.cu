@@ -397,26 +397,16 @@ __device__ __forceinline__ float interface_weight(const float rho[2], float2 cbu
     return 4.0f * c * (1.0f - c);
 }
 
-__device__ __forceinline__ void site_densities(const float* __restrict__ S, size_t n, size_t k, float rho[2]) {
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        float r = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) r += S[(size_t)(s * 9 + i) * n + k];
-        rho[s] = r;
-    }
-}
-
-// Per-block sums (FP64) of the limited density corrections, from the populations S
-// of the coarse run (FP32, [18][n]); mode 4: the sum of the order-parameter
-// corrections and the sum of the weights.
-__global__ void __launch_bounds__(256) drho_sum_kernel(const float* __restrict__ S, const float* __restrict__ y, size_t n,
-                                                       float4 oscale, int mode, float2 cbulk, double* __restrict__ part) {
+// Per-block sums (FP64) of the limited density corrections, from the densities
+// rho2 ([2][n], the sums of the FP32 populations); mode 4: the sum of the
+// order-parameter corrections and the sum of the weights.
+__global__ void __launch_bounds__(256) drho_sum_kernel(const float* __restrict__ rho2, const float* __restrict__ y,
+                                                       size_t n, float4 oscale, int mode, float2 cbulk,
+                                                       double* __restrict__ part) {
     __shared__ double red[2][8];
     double a = 0.0, b = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        float rho[2];
-        site_densities(S, n, k, rho);
+        const float rho[2] = {rho2[k], rho2[n + k]};
         const float w = interface_weight(rho, cbulk);
         float d[2];
         limited_drho(mode, rho, y[k] * oscale.x, y[n + k] * oscale.y, w, d);
@@ -611,16 +601,14 @@ lbm_status correct(lbm_closure* c, int mode) {
     const lbm_params& q = c->coarse_p;
     const double2 cbulk = make_double2(q.mass_A / (q.mass_A + q.minority * q.mass_B),
                                        q.minority * q.mass_A / (q.minority * q.mass_A + q.mass_B));
-    CL_STATUS(coarse_fields(c, c->raw));
-    lbm::normalize_kernel<<<512, 256, 0, c->stream>>>(c->raw, nullptr, c->nc, f4(c->in_mean), f4(c->in_scale),
-                                                      f4(c->out_scale), c->xin, nullptr);
-    CL_TRY(cudaGetLastError(), "normalize");
-    CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
-    // the FP32 copy of the coarse populations lives in the FP64 state buffer
+    // the FP32 copy of the coarse populations lives in the FP64 state buffer; the
+    // network's input comes from it (densities in the first half of raw)
     float* Sf = reinterpret_cast<float*>(c->S);
     CL_TRY(lbm::handle_pull_Sf(c->coarse, Sf), "pull coarse state");
+    CL_TRY(lbm::handle_closure_features(c->coarse, Sf, c->raw, c->in_mean, c->in_scale, c->xin), "network input");
+    CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
     const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
-    lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
+    lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(c->raw, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
     lbm::drho_total_kernel<<<1, 32, 0, c->stream>>>(c->part, kCorrBlocks);
     lbm::correct_kernel<<<kCorrBlocks * 4, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,

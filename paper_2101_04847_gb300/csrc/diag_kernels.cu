@@ -27,6 +27,8 @@
 // reuses T[0..3] for rho_A, rho_B, ux, uy as doubles.
 #include "lattice.cuh"
 
+#include <algorithm>
+
 namespace lbm {
 
 namespace {
@@ -441,7 +443,96 @@ cudaError_t moments(const DiagLaunch& D, const DiagArgs& a, cudaStream_t st) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// closure network input (FP32)
+// ---------------------------------------------------------------------------
+struct FeatArgs {
+    int nx, ny;
+    size_t n;
+    float G, gx, gw6[2], gext[2];
+    float mean[4], scale[4];
+};
+
+__global__ void __launch_bounds__(256) closure_density_kernel(const float* __restrict__ S, size_t n,
+                                                               float* __restrict__ rho2) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float r = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) r += S[(size_t)(s * 9 + i) * n + k];
+            rho2[(size_t)s * n + k] = r;
+        }
+}
+
+// sum_i w_i rho(x + c_i) c_i of one density field, zero beyond the walls
+__device__ __forceinline__ void nbr_sum_f(const float* __restrict__ r, const FeatArgs& a, int x, int y, float& sx,
+                                          float& sy) {
+    const int xm = x == 0 ? a.nx - 1 : x - 1;
+    const int xp = x == a.nx - 1 ? 0 : x + 1;
+    auto at = [&](int xx, int yy) { return (yy < 0 || yy >= a.ny) ? 0.0f : r[(size_t)yy * a.nx + xx]; };
+    const float E = at(xp, y), W = at(xm, y), N = at(x, y + 1), S = at(x, y - 1);
+    const float d = at(xp, y + 1) - at(xm, y - 1);
+    const float SE = at(xp, y - 1), NW = at(xm, y + 1);
+    sx = (E - W) * (1.0f / 9.0f) + (d + (SE - NW)) * (1.0f / 36.0f);
+    sy = (N - S) * (1.0f / 9.0f) + (d + (NW - SE)) * (1.0f / 36.0f);
+}
+
+// the same force and physical velocity as the diagnostics' velocity pass, in FP32
+__global__ void __launch_bounds__(256) closure_features_kernel(FeatArgs a, const float* __restrict__ S,
+                                                                const float* __restrict__ rho2, float* __restrict__ xo) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n; k += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k % a.nx);
+        float jx = 0.0f, jy = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const float f = S[(size_t)(s * 9 + i) * a.n + k];
+                jx += cx(i) * f;
+                jy += cy(i) * f;
+            }
+        const float rA = rho2[k], rB = rho2[a.n + k];
+        float nAx, nAy, nBx, nBy;
+        nbr_sum_f(rho2, a, x, y, nAx, nAy);
+        nbr_sum_f(rho2 + a.n, a, x, y, nBx, nBy);
+        float wA = 0.0f, wB = 0.0f;
+        if (y == 0) { wA += a.gw6[0]; wB += a.gw6[1]; }
+        if (y == a.ny - 1) { wA -= a.gw6[0]; wB -= a.gw6[1]; }
+        const float aAx = a.gx - a.G * nBx, aAy = (wA + a.gext[0]) - a.G * nBy;
+        const float aBx = a.gx - a.G * nAx, aBy = (wB + a.gext[1]) - a.G * nAy;
+        const float Fx = rA * aAx + rB * aBx, Fy = rA * aAy + rB * aBy;
+        const float rho = rA + rB;
+        const float ux = (jx + 0.5f * Fx) / rho, uy = (jy + 0.5f * Fy) / rho;
+        const float v[4] = {rA, rB, ux, uy};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xo[(size_t)c * a.n + k] = (v[c] - a.mean[c]) / a.scale[c];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_closure_features(const DiagLaunch& D, const float* S, float* rho2, const float mean[4],
+                                    const float scale[4], float* x, cudaStream_t st) {
+    FeatArgs a;
+    a.nx = D.grid.nx;
+    a.ny = D.grid.ny;
+    a.n = (size_t)a.nx * a.ny;
+    a.G = (float)D.G;
+    a.gx = (float)D.gx;
+    for (int s = 0; s < 2; ++s) {
+        a.gw6[s] = (float)(D.G_wall[s] / 6.0);
+        a.gext[s] = (float)D.g_ext[s];
+    }
+    for (int c = 0; c < 4; ++c) {
+        a.mean[c] = mean[c];
+        a.scale[c] = scale[c];
+    }
+    const int blocks = (int)std::min<size_t>(4096, (a.n + 255) / 256);
+    closure_density_kernel<<<blocks, 256, 0, st>>>(S, a.n, rho2);
+    closure_features_kernel<<<blocks, 256, 0, st>>>(a, S, rho2, x);
+    return cudaGetLastError();
+}
 
 size_t diag_scratch_doubles(int nx, int ny) { return (size_t)15 * nx * ny; }
 

@@ -326,6 +326,10 @@ cudaError_t handle_pull_Sf(lbm_handle* h, float* S) {
 cudaError_t handle_push_Sf(lbm_handle* h, const float* S) {
     return launch_push_from_float(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }
+cudaError_t handle_closure_features(lbm_handle* h, const float* S, float* rho2, const float mean[4],
+                                    const float scale[4], float* x) {
+    return launch_closure_features(diag_launch(h), S, rho2, mean, scale, x, h->stream);
+}
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed) {
     h->p.seed = seed;
     destroy_graphs(h);

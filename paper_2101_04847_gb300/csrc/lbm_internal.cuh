@@ -166,5 +166,13 @@ cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st);
 // rho_A, rho_B, ux, uy (double [ny][nx] each) into the scratch region at
 // diag_fields_offset (uses the whole scratch: 15 doubles per site)
 cudaError_t launch_fields(const DiagLaunch& D, double* fields, cudaStream_t st);
+// The closure network's input in FP32 from post-streaming populations S ([18][n],
+// as handle_pull_Sf writes them): rho_A, rho_B and the physical velocity
+// (j + F/2) / rho, each as (v - mean[c]) / scale[c], into x [4][n]; rho2 [2][n] is
+// scratch for the densities.
+cudaError_t launch_closure_features(const DiagLaunch& D, const float* S, float* rho2, const float mean[4],
+                                    const float scale[4], float* x, cudaStream_t st);
+cudaError_t handle_closure_features(lbm_handle* h, const float* S, float* rho2, const float mean[4],
+                                    const float scale[4], float* x);
 
 }  // namespace lbm
