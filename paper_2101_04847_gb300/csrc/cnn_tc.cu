@@ -2,30 +2,35 @@
 // shared memory staged by bulk asynchronous copies, FP32 accumulators in tensor
 // memory).
 //
-// One 3x3 convolution is an implicit GEMM per output row segment of 128 pixels:
-//   D[m][n] = sum over taps (ky, kx) and input channels c of
-//             A_(ky,kx)[m][c] * W[n][c][ky][kx],   A_(ky,kx)[m][c] = in[y + ky - 1][x0 + m + kx - 1][c]
-// with M = 128 pixels, N = 32 output channels (16 for the last layer, 4 of them
-// used) and K = 16 channels per MMA instruction.  A CTA owns a 128-pixel column
-// strip and a band of rows.  It streams the input rows of its band through a ring
-// of shared-memory slots, one row per slot with the channel groups of 8 as
-// separate planes of 136 pixels x 16 bytes, which is the tensor cores' K-major
-// layout without swizzle: 8 consecutive pixels form one 8x16-byte core matrix, the
-// next 8 pixels follow at 128 bytes (SBO) and the next 8 channels one plane further
-// (LBO).  The x shift of a tap is then just a 16-byte shift of the operand's start
-// address, so the 9 taps of a row read the same slots.  Weights are staged once
-// per CTA in the same layout (N rows of 16 bytes per channel group).
+// One 3x3 convolution is an implicit GEMM over row segments of 128 pixels.  The
+// three row taps are folded into N: for each staged input row r and x shift kx,
+//   D_r[m][ky W + n] += sum_c in[r][x0 + m + kx - 1][c] * w[n][c][ky][kx]
+// (M = 128 pixels, N = 3 W, W = 32 output channels, or 4 for the last layer with N
+// padded to 16; K = 16 channels per MMA instruction), and output row y is
+// D_(y-1)[., 0..W) + D_y[., W..2W) + D_(y+1)[., 2W..3W), summed in registers by the
+// epilogue as the rows stream past.  Each staged row is thus read by 3 x shifts x
+// (channels / 16) MMAs instead of 9 x (channels / 16): the tensor cores' reads of
+// shared memory, not DRAM, were the busiest unit with one tap per MMA.
+//
+// A CTA owns a 128-pixel column strip and a band of rows.  It streams the input
+// rows of its band (plus one above and below) through a ring of shared-memory
+// slots, one row per slot with the channel groups of 8 as separate planes of 136
+// pixels x 16 bytes, which is the tensor cores' K-major layout without swizzle: 8
+// consecutive pixels form one 8x16-byte core matrix, the next 8 pixels follow at
+// 128 bytes (SBO) and the next 8 channels one plane further (LBO).  The x shift of
+// a tap is then just a 16-byte shift of the operand's start address.  Weights are
+// staged once per CTA in the same layout (N rows of 16 bytes per channel group).
 //
 // Roles (6 warps): warp 0 lane 0 issues the bulk copies; warp 1 owns the tensor
-// memory (two accumulators of N columns, alternating between rows) and lane 0
-// issues the MMAs; warps 2-5 read the accumulators (warp w reads lanes
-// 32 (w mod 4) ... of tensor memory, i.e. pixels 32 (w mod 4) ...), add the bias,
-// apply ReLU, round to BF16 and store.  mbarriers: full[s] (copies landed),
-// empty[s] (MMAs reading slot s done, by tcgen05.commit), accf[b] (accumulator b
-// complete), acce[b] (accumulator b read).  Every wait is bounded: a wait that
-// gives up raises the status word, tells the other roles to stop, and the CTA
-// waits (again bounded) for its copies and MMAs in flight before freeing its
-// tensor memory.
+// memory (two accumulators of N columns, alternating between input rows) and lane
+// 0 issues the MMAs; warps 2-5 read the accumulators (warp w reads lanes
+// 32 (w mod 4) ... of tensor memory, i.e. pixels 32 (w mod 4) ...), complete one
+// output row per input row, add the bias, apply ReLU, round to BF16 and store.
+// mbarriers: full[s] (copies landed), empty[s] (MMAs reading slot s done, by
+// tcgen05.commit), accf[b] (accumulator b complete), acce[b] (accumulator b read).
+// Every wait is bounded: a wait that gives up raises the status word, tells the
+// other roles to stop, and the CTA waits (again bounded) for its copies and MMAs in
+// flight before freeing its tensor memory.
 #include "cnn_tc.cuh"
 
 #include <cuda_bf16.h>
@@ -51,8 +56,14 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Operand bytes of one layer's weights: 9 taps x (KG/2) K-steps x 2 groups x N rows x 16 B.
-__host__ __device__ constexpr int wbytes(int KG, int N) { return 9 * (KG / 2) * 2 * N * 16; }
+// Operand bytes of one layer's weights: 3 x shifts x (KG/2) K-steps x 2 groups x NF rows x 16 B.
+__host__ __device__ constexpr int wbytes(int KG, int NF) { return 3 * (KG / 2) * 2 * NF * 16; }
+// MMA width for W output channels per row tap: 3 W rounded up to a multiple of 16
+__host__ __device__ constexpr int nfold(int W) { return (3 * W + 15) / 16 * 16; }
+// tensor-memory columns of two accumulators (a power of two, at least 32)
+__host__ __device__ constexpr uint32_t tmem_cols(int NF) {
+    return 2 * NF <= 32 ? 32u : (2 * NF <= 64 ? 64u : (2 * NF <= 128 ? 128u : 256u));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -154,28 +165,39 @@ template <> __device__ __forceinline__ void tmem_load<16>(uint32_t t, float* v) 
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <> __device__ __forceinline__ void tmem_load<4>(uint32_t t, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(t));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int KG, int N> constexpr int smem_bytes() { return 256 + wbytes(KG, N) + kStages * KG * kPlane; }
+template <int KG, int NF> constexpr int smem_bytes() { return 256 + wbytes(KG, NF) + kStages * KG * kPlane; }
 
 // One 3x3 convolution layer.  KGG channel groups of 8 are read per input row
 // (KG >= KGG groups in shared memory, the extra ones zero: the first layer has 4
-// channels, padded to one group of 8 in memory and to K = 16 in the MMA).
-// HIDDEN: bias + ReLU, BF16 activation planes out; else bias, the first 4
-// channels as FP32 planes y[4][ny][nx].
-template <int KGG, int KG, int N, bool HIDDEN>
+// channels, padded to one group of 8 in memory and to K = 16 in the MMA).  W
+// output channels per row tap.  HIDDEN: bias + ReLU, BF16 activation planes out;
+// else bias, 4 channels as FP32 planes y[4][ny][nx].
+template <int KGG, int KG, int W, bool HIDDEN>
 __global__ void __launch_bounds__(kThreads, 1)
 conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, const float* __restrict__ bias,
                uint8_t* __restrict__ hout, float* __restrict__ yout, int nx, int ny, int pitch, int rows_per_cta,
                int* __restrict__ status) {
     constexpr int KSTEPS = KG / 2;
-    constexpr int WB = wbytes(KG, N);
+    constexpr int NF = nfold(W);
+    constexpr int WB = wbytes(KG, NF);
     constexpr int SLOT = KG * kPlane;
-    constexpr uint32_t NCOL = 2 * N >= 32 ? 2 * N : 32;
-    constexpr uint32_t ID = idesc(kM, N);
+    constexpr uint32_t NCOL = tmem_cols(NF);
+    constexpr uint32_t ID = idesc(kM, NF);
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
@@ -191,6 +213,7 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
     const int x0 = blockIdx.x * kM;
     const int y0 = blockIdx.y * rows_per_cta;
     const int R = min(rows_per_cta, ny - y0);
+    const int rows_in = R + 2;   // input rows y0 - 1 ... y0 + R
 
     for (int i = threadIdx.x; i < kStages * SLOT / 16; i += kThreads)
         reinterpret_cast<uint4*>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -220,11 +243,11 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0 && R > 0) {
-        // ---- producer: weights once, then the R + 2 input rows of the band
+        // ---- producer: weights once, then the input rows of the band
         mbar_expect_tx(wbar, WB);
         bulk_g2s(wsm, wop, WB, wbar);
         int j = 0;
-        for (; j < R + 2; ++j) {
+        for (; j < rows_in; ++j) {
             const int s = j % kStages;
             if (j >= kStages && !mbar_wait(&empty[s], (uint32_t)((j / kStages) - 1) & 1u)) {
                 *stop = 1;
@@ -242,51 +265,49 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
             if (!mbar_wait(&full[q % kStages], (uint32_t)(q / kStages) & 1u)) atomicOr(status, 2);
         mbar_wait(wbar, 0);
     } else if (warp == 1 && lane == 0 && R > 0) {
-        // ---- MMA issuer
+        // ---- MMA issuer: one accumulator per input row
         bool ok = mbar_wait(wbar, 0);
-        int k = 0;
-        for (; ok && k < R; ++k) {
-            if (k == 0) ok = mbar_wait(&full[0], 0) && mbar_wait(&full[1 % kStages], (1 / kStages) & 1);
-            if (ok) ok = mbar_wait(&full[(k + 2) % kStages], (uint32_t)((k + 2) / kStages) & 1u);
-            if (ok && k >= 2) ok = mbar_wait(&acce[k & 1], (uint32_t)((k >> 1) - 1) & 1u);
+        int j = 0;
+        for (; ok && j < rows_in; ++j) {
+            ok = mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
+            if (ok && j >= 2) ok = mbar_wait(&acce[j & 1], (uint32_t)((j >> 1) - 1) & 1u);
             if (!ok || *stop) break;
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)((k & 1) * N);
+            const uint32_t d = tmem + (uint32_t)((j & 1) * NF);
+            const uint32_t slot = smem_u32(ring + (j % kStages) * SLOT);
             uint32_t acc = 0;
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                const uint32_t slot = smem_u32(ring + ((k + ky) % kStages) * SLOT);
+            for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                    for (int s = 0; s < KSTEPS; ++s) {
-                        const uint64_t a = sdesc(slot + (uint32_t)(2 * s * kPlane + kx * 16), kPlane, 128);
-                        const uint64_t b =
-                            sdesc(smem_u32(wsm) + (uint32_t)((((ky * 3 + kx) * KSTEPS + s) * 2 * N) * 16), N * 16, 128);
-                        mma_bf16(d, a, b, ID, acc);
-                        acc = 1;
-                    }
-            }
-            mma_commit(&accf[k & 1]);
-            mma_commit(&empty[k % kStages]);
+                for (int s = 0; s < KSTEPS; ++s) {
+                    const uint64_t a = sdesc(slot + (uint32_t)(2 * s * kPlane + kx * 16), kPlane, 128);
+                    const uint64_t b = sdesc(smem_u32(wsm) + (uint32_t)(((kx * KSTEPS + s) * 2 * NF) * 16), NF * 16, 128);
+                    mma_bf16(d, a, b, ID, acc);
+                    acc = 1;
+                }
+            mma_commit(&accf[j & 1]);
+            mma_commit(&empty[j % kStages]);
         }
         if (!ok) {
             *stop = 1;
             atomicOr(status, 4);
         }
         // the MMAs issued last are done before anyone frees the tensor memory
-        if (k > 0 && !mbar_wait(&accf[(k - 1) & 1], (uint32_t)((k - 1) >> 1) & 1u)) atomicOr(status, 8);
+        if (j > 0 && !mbar_wait(&accf[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u)) atomicOr(status, 8);
     } else if (warp >= 2 && R > 0) {
-        // ---- epilogue: pixel m of the strip = TMEM lane 32 (warp mod 4) + lane
+        // ---- epilogue: pixel m of the strip = TMEM lane 32 (warp mod 4) + lane.
+        // Before input row j: T1 = output row j - 2 without its last tap row,
+        // T2 = output row j - 1 with its first only (band indices).
+        constexpr int L = HIDDEN ? W : kOut;   // channels read back per row tap
         const int q = warp & 3;
         const int m = q * 32 + lane;
         const int x = x0 + m;
-        float bv[N];
+        float T1[L], T2[L], O[L];
 #pragma unroll
-        for (int n = 0; n < N; ++n) bv[n] = (HIDDEN || n < kOut) ? __ldg(bias + n) : 0.0f;
-        for (int k = 0; k < R; ++k) {
+        for (int n = 0; n < L; ++n) T1[n] = T2[n] = 0.0f;
+        for (int j = 0; j < rows_in; ++j) {
             if (__any_sync(0xffffffffu, *stop != 0)) break;
-            const bool mine = mbar_wait(&accf[k & 1], (uint32_t)(k >> 1) & 1u);
+            const bool mine = mbar_wait(&accf[j & 1], (uint32_t)(j >> 1) & 1u);
             if (!__all_sync(0xffffffffu, mine)) {
                 if (lane == 0) {
                     *stop = 1;
@@ -295,18 +316,25 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
                 break;
             }
             tc_fence_after();
-            float v[N];
-            tmem_load<N>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((k & 1) * N), v);
+            const uint32_t t = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((j & 1) * NF);
+            tmem_load<L>(t + 2 * W, O);        // third row tap: output row j - 2 is complete
+#pragma unroll
+            for (int n = 0; n < L; ++n) O[n] += T1[n];
+            tmem_load<L>(t + W, T1);           // second row tap of output row j - 1
+#pragma unroll
+            for (int n = 0; n < L; ++n) T1[n] += T2[n];
+            tmem_load<L>(t, T2);               // first row tap of output row j
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[k & 1]);
-            const int y = y0 + k;
-            if (x < nx) {
+            if (lane == 0) mbar_arrive(&acce[j & 1]);
+            const int y = y0 + j - 2;
+            if (j >= 2 && x < nx) {
                 if constexpr (HIDDEN) {
-                    uint32_t pk[N / 2];
+                    uint32_t pk[W / 2];
 #pragma unroll
-                    for (int n = 0; n < N / 2; ++n)
-                        pk[n] = pack_bf16(fmaxf(v[2 * n] + bv[2 * n], 0.0f), fmaxf(v[2 * n + 1] + bv[2 * n + 1], 0.0f));
+                    for (int n = 0; n < W / 2; ++n)
+                        pk[n] = pack_bf16(fmaxf(O[2 * n] + __ldg(bias + 2 * n), 0.0f),
+                                          fmaxf(O[2 * n + 1] + __ldg(bias + 2 * n + 1), 0.0f));
                     const size_t row = (size_t)(y + 1) * 4 * pitch;
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
@@ -319,7 +347,7 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
                 } else {
                     const size_t n = (size_t)nx * ny;
 #pragma unroll
-                    for (int c = 0; c < kOut; ++c) yout[(size_t)c * n + (size_t)y * nx + x] = v[c] + bv[c];
+                    for (int c = 0; c < kOut; ++c) yout[(size_t)c * n + (size_t)y * nx + x] = O[c] + __ldg(bias + c);
                 }
             }
         }
@@ -333,19 +361,21 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
     }
 }
 
-// Weights of one layer into the operand layout: [tap][K-step][group j][row n][8],
-// channel c = (2 K-step + j) * 8 + e; zero for c >= cin or n >= cout.
-__global__ void weights_kernel(const float* __restrict__ w, int cin, int cout, int ksteps, int N,
+// Weights of one layer into the operand layout: [kx][K-step][group j][row n'][8]
+// with row n' = ky W + n (the three row taps side by side) and channel
+// c = (2 K-step + j) * 8 + e; zero for c >= cin, n >= cout or n' >= 3 W.
+__global__ void weights_kernel(const float* __restrict__ w, int cin, int cout, int ksteps, int W, int NF,
                                __nv_bfloat16* __restrict__ out) {
-    const int total = 9 * ksteps * 2 * N * 8;
+    const int total = 3 * ksteps * 2 * NF * 8;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int e = i & 7;
-        const int n = (i >> 3) % N;
-        const int j = (i / (8 * N)) & 1;
-        const int s = (i / (16 * N)) % ksteps;
-        const int t = i / (16 * N * ksteps);
+        const int np = (i >> 3) % NF;
+        const int j = (i / (8 * NF)) & 1;
+        const int s = (i / (16 * NF)) % ksteps;
+        const int kx = i / (16 * NF * ksteps);
+        const int ky = np / W, n = np % W;
         const int c = (2 * s + j) * 8 + e;
-        const float v = (c < cin && n < cout) ? w[(n * cin + c) * 9 + t] : 0.0f;
+        const float v = (c < cin && n < cout && ky < 3) ? w[(n * cin + c) * 9 + ky * 3 + kx] : 0.0f;
         out[i] = __float2bfloat16_rn(v);
     }
 }
@@ -383,11 +413,11 @@ struct Launch {
 };
 
 // Bands of rows so that all CTAs of a layer are resident at once.
-template <int KGG, int KG, int N, bool HIDDEN>
+template <int KGG, int KG, int W, bool HIDDEN>
 cudaError_t launch_conv(const Bufs& B, const uint8_t* in, const uint8_t* w, const float* bias, uint8_t* hout,
                         float* yout, cudaStream_t st) {
-    constexpr int SM = smem_bytes<KG, N>();
-    auto kern = conv_tc_kernel<KGG, KG, N, HIDDEN>;
+    constexpr int SM = smem_bytes<KG, nfold(W)>();
+    auto kern = conv_tc_kernel<KGG, KG, W, HIDDEN>;
     static bool configured = false;
     static int per_sm = 1, sms = 1;
     if (!configured) {
@@ -407,8 +437,7 @@ cudaError_t launch_conv(const Bufs& B, const uint8_t* in, const uint8_t* w, cons
         e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
         const int regs = (std::max(fa.numRegs, 1) + 7) / 8 * 8 * kThreads;
-        per_sm = std::min({smem_sm / (SM + 1024), regs_sm / regs, thr_sm / kThreads,
-                           512 / (int)(2 * N >= 32 ? 2 * N : 32)});
+        per_sm = std::min({smem_sm / (SM + 1024), regs_sm / regs, thr_sm / kThreads, 512 / (int)tmem_cols(nfold(W))});
         per_sm = std::max(1, per_sm);
         configured = true;
     }
@@ -416,7 +445,7 @@ cudaError_t launch_conv(const Bufs& B, const uint8_t* in, const uint8_t* w, cons
     int groups = std::max(1, slots / B.tiles_x);
     int rows = std::max(1, (B.ny + groups - 1) / groups);
     groups = (B.ny + rows - 1) / rows;
-    conv_tc_kernel<KGG, KG, N, HIDDEN><<<dim3(B.tiles_x, groups), kThreads, SM, st>>>(in, w, bias, hout, yout, B.nx,
+    conv_tc_kernel<KGG, KG, W, HIDDEN><<<dim3(B.tiles_x, groups), kThreads, SM, st>>>(in, w, bias, hout, yout, B.nx,
                                                                                       B.ny, B.pitch, rows, B.status);
     return cudaGetLastError();
 }
@@ -427,8 +456,8 @@ size_t bytes(int nx, int ny) {
     const int tiles = (nx + kM - 1) / kM;
     const size_t pitch = (size_t)tiles * kM + 2;
     const size_t rows = (size_t)ny + 2;
-    return align256(rows * pitch * 16) + 2 * align256(rows * 4 * pitch * 16) + align256(wbytes(2, 32)) +
-           align256(wbytes(4, 32)) + align256(wbytes(4, 16)) + 256;
+    return align256(rows * pitch * 16) + 2 * align256(rows * 4 * pitch * 16) + align256(wbytes(2, nfold(32))) +
+           align256(wbytes(4, nfold(32))) + align256(wbytes(4, nfold(kOut))) + 256;
 }
 
 Bufs carve(void* base, int nx, int ny) {
@@ -442,17 +471,17 @@ Bufs carve(void* base, int nx, int ny) {
     B.xin = p; p += align256(rows * B.pitch * 16);
     B.h1 = p; p += align256(rows * 4 * B.pitch * 16);
     B.h2 = p; p += align256(rows * 4 * B.pitch * 16);
-    B.w1 = p; p += align256(wbytes(2, 32));
-    B.w2 = p; p += align256(wbytes(4, 32));
-    B.w3 = p; p += align256(wbytes(4, 16));
+    B.w1 = p; p += align256(wbytes(2, nfold(32)));
+    B.w2 = p; p += align256(wbytes(4, nfold(32)));
+    B.w3 = p; p += align256(wbytes(4, nfold(kOut)));
     B.status = reinterpret_cast<int*>(p);
     return B;
 }
 
 cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st) {
-    weights_kernel<<<8, 256, 0, st>>>(params + kW1, kIn, kHid, 1, 32, reinterpret_cast<__nv_bfloat16*>(B.w1));
-    weights_kernel<<<16, 256, 0, st>>>(params + kW2, kHid, kHid, 2, 32, reinterpret_cast<__nv_bfloat16*>(B.w2));
-    weights_kernel<<<8, 256, 0, st>>>(params + kW3, kHid, kOut, 2, 16, reinterpret_cast<__nv_bfloat16*>(B.w3));
+    weights_kernel<<<8, 256, 0, st>>>(params + kW1, kIn, kHid, 1, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w1));
+    weights_kernel<<<16, 256, 0, st>>>(params + kW2, kHid, kHid, 2, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w2));
+    weights_kernel<<<4, 256, 0, st>>>(params + kW3, kHid, kOut, 2, kOut, nfold(kOut), reinterpret_cast<__nv_bfloat16*>(B.w3));
     const size_t px = (size_t)(B.ny + 2) * B.pitch;
     const int blocks = (int)std::min<size_t>(4096, (px + 255) / 256);
     prep_kernel<<<blocks, 256, 0, st>>>(x, B.nx, B.ny, B.pitch, B.xin, B.h1, B.h2, B.status);
@@ -462,7 +491,7 @@ cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, 
     if (e != cudaSuccess) return e;
     e = launch_conv<4, 4, 32, true>(B, B.h1, B.w2, params + kB2, B.h2, nullptr, st);
     if (e != cudaSuccess) return e;
-    return launch_conv<4, 4, 16, false>(B, B.h2, B.w3, params + kB3, nullptr, y, st);
+    return launch_conv<4, 4, kOut, false>(B, B.h2, B.w3, params + kB3, nullptr, y, st);
 }
 
 cudaError_t status(const Bufs& B, cudaStream_t st, int* out) {
