@@ -266,6 +266,14 @@ lbm_status lbm_cnn_infer(const float* params, const float* x, int32_t nx, int32_
  * this workspace gave up (its output is then incomplete), else LBM_OK. */
 lbm_status lbm_cnn_infer_status(void* workspace, int32_t nx, int32_t ny, void* cuda_stream);
 
+/* Test of the timeout path (no counterpart in the paper): lbm_cnn_infer with the
+ * kernels' bulk copies withheld and their waits limited to a few thousand polls,
+ * so every wait gives up, raises the status word and the kernels return (y is
+ * left incomplete).  lbm_cnn_infer_status then reports LBM_ETIMEOUT; the next
+ * lbm_cnn_infer clears the status. */
+lbm_status lbm_cnn_infer_test_timeout(const float* params, const float* x, int32_t nx, int32_t ny, void* workspace,
+                                      size_t ws_bytes, void* cuda_stream, float* y);
+
 /* loss = mean((CNN(x) - t)^2) over the 4*ny*nx outputs (host), grad = dloss/dparams
  * (device, LBM_CNN_PARAMS floats).  Synchronises the stream. */
 lbm_status lbm_cnn_loss_grad(const float* params, const float* x, const float* t, int32_t nx, int32_t ny,

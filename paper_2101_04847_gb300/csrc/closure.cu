@@ -646,6 +646,15 @@ lbm_status lbm_cnn_infer(const float* params, const float* x, int32_t nx, int32_
     return LBM_OK;
 }
 
+lbm_status lbm_cnn_infer_test_timeout(const float* params, const float* x, int32_t nx, int32_t ny, void* ws,
+                                      size_t ws_bytes, void* stream, float* y) {
+    if (!params || !x || !ws || !y || nx < 1 || ny < 1) return cl_fail(LBM_EINVAL, "NULL argument or empty grid");
+    if (ws_bytes < lbm::cnn::workspace_bytes(nx, ny)) return cl_fail(LBM_ENOMEM, "CNN workspace too small");
+    lbm::cnn::Net N = lbm::cnn::carve(ws, nx, ny);
+    CL_TRY(lbm::cnn_tc::infer(N.tc, params, x, y, (cudaStream_t)stream, true), "cnn inference (copies withheld)");
+    return LBM_OK;
+}
+
 lbm_status lbm_cnn_infer_status(void* ws, int32_t nx, int32_t ny, void* stream) {
     if (!ws || nx < 1 || ny < 1) return cl_fail(LBM_EINVAL, "NULL workspace or empty grid");
     lbm::cnn::Net N = lbm::cnn::carve(ws, nx, ny);

@@ -86,8 +86,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -191,7 +191,11 @@ template <int KGG, int KG, int W, bool HIDDEN>
 __global__ void __launch_bounds__(kThreads, 1)
 conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, const float* __restrict__ bias,
                uint8_t* __restrict__ hout, float* __restrict__ yout, int nx, int ny, int pitch, int rows_per_cta,
-               int* __restrict__ status) {
+               int* __restrict__ status, int withhold) {
+    // withhold != 0 (tests of the timeout path only): no copies are issued and every
+    // wait polls 4096 times, so the waits of the MMA issuer and of the epilogue give
+    // up, raise the status word and the CTA returns
+    const uint32_t lim = withhold ? 4096u : kWaitLimit;
     constexpr int KSTEPS = KG / 2;
     constexpr int NF = nfold(W);
     constexpr int WB = wbytes(KG, NF);
@@ -242,7 +246,7 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0 && R > 0) {
+    if (warp == 0 && lane == 0 && R > 0 && !withhold) {
         // ---- producer: weights once, then the input rows of the band
         mbar_expect_tx(wbar, WB);
         bulk_g2s(wsm, wop, WB, wbar);
@@ -266,11 +270,11 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
         mbar_wait(wbar, 0);
     } else if (warp == 1 && lane == 0 && R > 0) {
         // ---- MMA issuer: one accumulator per input row
-        bool ok = mbar_wait(wbar, 0);
+        bool ok = mbar_wait(wbar, 0, lim);
         int j = 0;
         for (; ok && j < rows_in; ++j) {
-            ok = mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
-            if (ok && j >= 2) ok = mbar_wait(&acce[j & 1], (uint32_t)((j >> 1) - 1) & 1u);
+            ok = mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, lim);
+            if (ok && j >= 2) ok = mbar_wait(&acce[j & 1], (uint32_t)((j >> 1) - 1) & 1u, lim);
             if (!ok || *stop) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)((j & 1) * NF);
@@ -293,7 +297,7 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
             atomicOr(status, 4);
         }
         // the MMAs issued last are done before anyone frees the tensor memory
-        if (j > 0 && !mbar_wait(&accf[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u)) atomicOr(status, 8);
+        if (j > 0 && !mbar_wait(&accf[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u, lim)) atomicOr(status, 8);
     } else if (warp >= 2 && R > 0) {
         // ---- epilogue: pixel m of the strip = TMEM lane 32 (warp mod 4) + lane.
         // Before input row j: T1 = output row j - 2 without its last tap row,
@@ -307,7 +311,7 @@ conv_tc_kernel(const uint8_t* __restrict__ in, const uint8_t* __restrict__ wop, 
         for (int n = 0; n < L; ++n) T1[n] = T2[n] = 0.0f;
         for (int j = 0; j < rows_in; ++j) {
             if (__any_sync(0xffffffffu, *stop != 0)) break;
-            const bool mine = mbar_wait(&accf[j & 1], (uint32_t)(j >> 1) & 1u);
+            const bool mine = mbar_wait(&accf[j & 1], (uint32_t)(j >> 1) & 1u, lim);
             if (!__all_sync(0xffffffffu, mine)) {
                 if (lane == 0) {
                     *stop = 1;
@@ -415,7 +419,7 @@ struct Launch {
 // Bands of rows so that all CTAs of a layer are resident at once.
 template <int KGG, int KG, int W, bool HIDDEN>
 cudaError_t launch_conv(const Bufs& B, const uint8_t* in, const uint8_t* w, const float* bias, uint8_t* hout,
-                        float* yout, cudaStream_t st) {
+                        float* yout, cudaStream_t st, int withhold) {
     constexpr int SM = smem_bytes<KG, nfold(W)>();
     auto kern = conv_tc_kernel<KGG, KG, W, HIDDEN>;
     static bool configured = false;
@@ -446,7 +450,8 @@ cudaError_t launch_conv(const Bufs& B, const uint8_t* in, const uint8_t* w, cons
     int rows = std::max(1, (B.ny + groups - 1) / groups);
     groups = (B.ny + rows - 1) / rows;
     conv_tc_kernel<KGG, KG, W, HIDDEN><<<dim3(B.tiles_x, groups), kThreads, SM, st>>>(in, w, bias, hout, yout, B.nx,
-                                                                                      B.ny, B.pitch, rows, B.status);
+                                                                                      B.ny, B.pitch, rows, B.status,
+                                                                                      withhold);
     return cudaGetLastError();
 }
 
@@ -478,7 +483,8 @@ Bufs carve(void* base, int nx, int ny) {
     return B;
 }
 
-cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st) {
+cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st, bool withhold) {
+    const int wh = withhold ? 1 : 0;
     weights_kernel<<<8, 256, 0, st>>>(params + kW1, kIn, kHid, 1, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w1));
     weights_kernel<<<16, 256, 0, st>>>(params + kW2, kHid, kHid, 2, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w2));
     weights_kernel<<<4, 256, 0, st>>>(params + kW3, kHid, kOut, 2, kOut, nfold(kOut), reinterpret_cast<__nv_bfloat16*>(B.w3));
@@ -487,11 +493,11 @@ cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, 
     prep_kernel<<<blocks, 256, 0, st>>>(x, B.nx, B.ny, B.pitch, B.xin, B.h1, B.h2, B.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_conv<1, 2, 32, true>(B, B.xin, B.w1, params + kB1, B.h1, nullptr, st);
+    e = launch_conv<1, 2, 32, true>(B, B.xin, B.w1, params + kB1, B.h1, nullptr, st, wh);
     if (e != cudaSuccess) return e;
-    e = launch_conv<4, 4, 32, true>(B, B.h1, B.w2, params + kB2, B.h2, nullptr, st);
+    e = launch_conv<4, 4, 32, true>(B, B.h1, B.w2, params + kB2, B.h2, nullptr, st, wh);
     if (e != cudaSuccess) return e;
-    return launch_conv<4, 4, kOut, false>(B, B.h2, B.w3, params + kB3, nullptr, y, st);
+    return launch_conv<4, 4, kOut, false>(B, B.h2, B.w3, params + kB3, nullptr, y, st, wh);
 }
 
 cudaError_t status(const Bufs& B, cudaStream_t st, int* out) {

@@ -30,7 +30,10 @@ struct Bufs {
 size_t bytes(int nx, int ny);
 Bufs carve(void* base, int nx, int ny);
 // y[4][ny][nx] = CNN(x[4][ny][nx]); params as in the FP32 path.  Asynchronous.
-cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st);
+// withhold (tests of the timeout path only): the kernels issue no copies and poll
+// briefly, so their waits give up and raise the status word.
+cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st,
+                  bool withhold = false);
 // Reads the status word (synchronises the stream): 0 if every wait completed.
 cudaError_t status(const Bufs& B, cudaStream_t st, int* out);
 

@@ -85,6 +85,8 @@ _PROTOS = {
     "lbm_cnn_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
                                 C.c_void_p, C.c_void_p]),
     "lbm_cnn_infer_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    "lbm_cnn_infer_test_timeout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
+                                             C.c_void_p, C.c_void_p]),
     "lbm_cnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                     C.c_size_t, C.c_void_p, _P(C.c_double), C.c_void_p]),
     "lbm_closure_coarse_params": (C.c_int, [_P(LbmParams), _P(LbmParams)]),
@@ -397,6 +399,10 @@ class Cnn:
 
     def infer(self, params, x, y):
         _check(self.lib.lbm_cnn_infer(*self._args(params, x, y)), "lbm_cnn_infer")
+
+    def infer_test_timeout(self, params, x, y):
+        """Tests of the timeout path: the inference kernels with their copies withheld."""
+        _check(self.lib.lbm_cnn_infer_test_timeout(*self._args(params, x, y)), "lbm_cnn_infer_test_timeout")
 
     def status(self):
         _check(self.lib.lbm_cnn_infer_status(C.c_void_p(self.ws.data_ptr()), self.nx, self.ny, self._st()),

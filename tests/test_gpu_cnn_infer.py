@@ -116,3 +116,25 @@ def test_infer_full_size_sampled(gpu):
         assert np.all(np.abs(g - ref) <= bound + 1e-7 * scale), (ya, xa)
         assert np.mean(np.abs(g - emu) > 1e-5 * scale) <= 0.05, (ya, xa)
         assert np.max(np.abs(g - emu)) <= one_flip + 1e-5 * scale, (ya, xa)
+
+
+def test_a_wait_that_gives_up_is_reported_and_the_context_stays_usable(gpu):
+    # the kernels' copies are withheld: every wait gives up after a few thousand
+    # polls, the status word is raised and read on the host; a normal call after it
+    # runs and is correct
+    import torch
+
+    nx, ny = 300, 70
+    p32 = _params(5)
+    x = np.random.default_rng(6).normal(size=(4, ny, nx)).astype(np.float32)
+    cnn = lbm.Cnn(nx, ny)
+    dp = torch.from_numpy(p32).cuda()
+    dx = torch.from_numpy(x).cuda()
+    dy = torch.zeros_like(dx)
+    cnn.infer_test_timeout(dp, dx, dy)
+    with pytest.raises(lbm.LbmError) as err:
+        cnn.status()
+    assert err.value.status == lbm.LBM_ETIMEOUT
+    cnn.infer(dp, dx, dy)
+    cnn.status()
+    check_against_oracle(dy.double().cpu().numpy(), oracle_view(p32), x.astype(np.float64))
