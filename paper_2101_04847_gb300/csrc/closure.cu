@@ -397,6 +397,38 @@ __device__ __forceinline__ float interface_weight(const float rho[2], float2 cbu
     return 4.0f * c * (1.0f - c);
 }
 
+// Gather of the coarse run's populations after streaming (as the step kernels pull
+// them) into FP32 S [18][n], with the densities rho2 [2][n] and the total momenta
+// j2 [2][n] that the network input and the mass sums need.
+template <typename T>
+__global__ void closure_pull_kernel(const T* __restrict__ fin, Grid g, float sA, float sB, float* __restrict__ S,
+                                    float* __restrict__ rho2, float* __restrict__ j2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const float shift[2] = {sA, sB};
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9];
+    pull_site<T>(fin, g, shift, y, x, xm, xp, f);
+    const size_t n = (size_t)g.nx * g.ny, k = (size_t)y * g.nx + x;
+    float jx = 0.0f, jy = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float r = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S[(size_t)(s * 9 + i) * n + k] = f[s][i];
+            r += f[s][i];
+            jx += cx(i) * f[s][i];
+            jy += cy(i) * f[s][i];
+        }
+        rho2[(size_t)s * n + k] = r;
+    }
+    j2[k] = jx;
+    j2[n + k] = jy;
+}
+
 // Per-block sums (FP64) of the limited density corrections, from the densities
 // rho2 ([2][n], the sums of the FP32 populations); mode 4: the sum of the
 // order-parameter corrections and the sum of the weights.
@@ -596,19 +628,39 @@ lbm_status set_coarse(lbm_closure* c, const float* fld) {
 // apply the network's correction to the coarse run (mode 1: densities and velocity,
 // mode 2: order parameter only, mode 3: order parameter and a quarter of the velocity,
 // mode 4: as mode 3 with the order parameter corrected on the interface only)
+cudaError_t launch_closure_pull(const lbm::PopView& v, float* S, float* rho2, float* j2) {
+    dim3 grid((v.grid.nx + 127) / 128, v.grid.ny);
+    switch (v.storage) {
+        case LBM_STORE_F16:
+            lbm::closure_pull_kernel<__half><<<grid, 128, 0, v.stream>>>((const __half*)v.fin, v.grid, v.shift[0],
+                                                                         v.shift[1], S, rho2, j2);
+            break;
+        case LBM_STORE_BF16:
+            lbm::closure_pull_kernel<__nv_bfloat16><<<grid, 128, 0, v.stream>>>((const __nv_bfloat16*)v.fin, v.grid,
+                                                                                v.shift[0], v.shift[1], S, rho2, j2);
+            break;
+        default:
+            lbm::closure_pull_kernel<float><<<grid, 128, 0, v.stream>>>((const float*)v.fin, v.grid, v.shift[0],
+                                                                        v.shift[1], S, rho2, j2);
+    }
+    return cudaGetLastError();
+}
+
 lbm_status correct(lbm_closure* c, int mode) {
     // bulk mass fractions of the coarse run's initial state (pure A on top, pure B below)
     const lbm_params& q = c->coarse_p;
     const double2 cbulk = make_double2(q.mass_A / (q.mass_A + q.minority * q.mass_B),
                                        q.minority * q.mass_A / (q.minority * q.mass_A + q.mass_B));
-    // the FP32 copy of the coarse populations lives in the FP64 state buffer; the
-    // network's input comes from it (densities in the first half of raw)
+    // the FP32 copy of the coarse populations lives in the FP64 state buffer; raw
+    // holds the densities (first half) and the momenta (second half)
     float* Sf = reinterpret_cast<float*>(c->S);
-    CL_TRY(lbm::handle_pull_Sf(c->coarse, Sf), "pull coarse state");
-    CL_TRY(lbm::handle_closure_features(c->coarse, Sf, c->raw, c->in_mean, c->in_scale, c->xin), "network input");
+    float* rho2 = c->raw;
+    float* j2 = c->raw + 2 * c->nc;
+    CL_TRY(launch_closure_pull(lbm::handle_pops(c->coarse), Sf, rho2, j2), "pull coarse state");
+    CL_TRY(lbm::handle_closure_features(c->coarse, rho2, j2, c->in_mean, c->in_scale, c->xin), "network input");
     CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
     const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
-    lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(c->raw, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
+    lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(rho2, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
     lbm::drho_total_kernel<<<1, 32, 0, c->stream>>>(c->part, kCorrBlocks);
     lbm::correct_kernel<<<kCorrBlocks * 4, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,

@@ -453,18 +453,6 @@ struct FeatArgs {
     float mean[4], scale[4];
 };
 
-__global__ void __launch_bounds__(256) closure_density_kernel(const float* __restrict__ S, size_t n,
-                                                               float* __restrict__ rho2) {
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            float r = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) r += S[(size_t)(s * 9 + i) * n + k];
-            rho2[(size_t)s * n + k] = r;
-        }
-}
-
 // sum_i w_i rho(x + c_i) c_i of one density field, zero beyond the walls
 __device__ __forceinline__ void nbr_sum_f(const float* __restrict__ r, const FeatArgs& a, int x, int y, float& sx,
                                           float& sy) {
@@ -479,19 +467,11 @@ __device__ __forceinline__ void nbr_sum_f(const float* __restrict__ r, const Fea
 }
 
 // the same force and physical velocity as the diagnostics' velocity pass, in FP32
-__global__ void __launch_bounds__(256) closure_features_kernel(FeatArgs a, const float* __restrict__ S,
-                                                                const float* __restrict__ rho2, float* __restrict__ xo) {
+__global__ void __launch_bounds__(256) closure_features_kernel(FeatArgs a, const float* __restrict__ rho2,
+                                                                const float* __restrict__ j2, float* __restrict__ xo) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n; k += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(k / a.nx), x = (int)(k % a.nx);
-        float jx = 0.0f, jy = 0.0f;
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const float f = S[(size_t)(s * 9 + i) * a.n + k];
-                jx += cx(i) * f;
-                jy += cy(i) * f;
-            }
+        const float jx = j2[k], jy = j2[a.n + k];
         const float rA = rho2[k], rB = rho2[a.n + k];
         float nAx, nAy, nBx, nBy;
         nbr_sum_f(rho2, a, x, y, nAx, nAy);
@@ -512,7 +492,7 @@ __global__ void __launch_bounds__(256) closure_features_kernel(FeatArgs a, const
 
 }  // namespace
 
-cudaError_t launch_closure_features(const DiagLaunch& D, const float* S, float* rho2, const float mean[4],
+cudaError_t launch_closure_features(const DiagLaunch& D, const float* rho2, const float* j2, const float mean[4],
                                     const float scale[4], float* x, cudaStream_t st) {
     FeatArgs a;
     a.nx = D.grid.nx;
@@ -529,8 +509,7 @@ cudaError_t launch_closure_features(const DiagLaunch& D, const float* S, float* 
         a.scale[c] = scale[c];
     }
     const int blocks = (int)std::min<size_t>(4096, (a.n + 255) / 256);
-    closure_density_kernel<<<blocks, 256, 0, st>>>(S, a.n, rho2);
-    closure_features_kernel<<<blocks, 256, 0, st>>>(a, S, rho2, x);
+    closure_features_kernel<<<blocks, 256, 0, st>>>(a, rho2, j2, x);
     return cudaGetLastError();
 }
 

@@ -320,15 +320,22 @@ cudaError_t handle_pull_S(lbm_handle* h, double* S) {
 cudaError_t handle_push_S(lbm_handle* h, const double* S) {
     return launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }
-cudaError_t handle_pull_Sf(lbm_handle* h, float* S) {
-    return launch_pull_to_float(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream);
+PopView handle_pops(lbm_handle* h) {
+    PopView v;
+    v.fin = h->pops(h->cur);
+    v.grid = h->grid;
+    v.storage = h->p.storage;
+    v.shift[0] = h->shift[0];
+    v.shift[1] = h->shift[1];
+    v.stream = h->stream;
+    return v;
 }
 cudaError_t handle_push_Sf(lbm_handle* h, const float* S) {
     return launch_push_from_float(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }
-cudaError_t handle_closure_features(lbm_handle* h, const float* S, float* rho2, const float mean[4],
+cudaError_t handle_closure_features(lbm_handle* h, const float* rho2, const float* j2, const float mean[4],
                                     const float scale[4], float* x) {
-    return launch_closure_features(diag_launch(h), S, rho2, mean, scale, x, h->stream);
+    return launch_closure_features(diag_launch(h), rho2, j2, mean, scale, x, h->stream);
 }
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed) {
     h->p.seed = seed;

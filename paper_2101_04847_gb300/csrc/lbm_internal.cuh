@@ -116,8 +116,16 @@ cudaError_t handle_restore_state(lbm_handle* h);
 cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy);
 cudaError_t handle_pull_S(lbm_handle* h, double* S);
 cudaError_t handle_push_S(lbm_handle* h, const double* S);
-cudaError_t handle_pull_Sf(lbm_handle* h, float* S);         // as handle_pull_S, FP32 copy
-cudaError_t handle_push_Sf(lbm_handle* h, const float* S);
+cudaError_t handle_push_Sf(lbm_handle* h, const float* S);   // as handle_push_S, from FP32
+// A handle's current populations as the closure's gather kernel reads them.
+struct PopView {
+    const void* fin;
+    Grid grid;
+    int storage;
+    float shift[2];
+    cudaStream_t stream;
+};
+PopView handle_pops(lbm_handle* h);
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed);
 
 // message returned by lbm_last_error() on this thread (lbm_api.cu)
@@ -166,13 +174,13 @@ cudaError_t launch_diagnostics(const DiagLaunch& D, cudaStream_t st);
 // rho_A, rho_B, ux, uy (double [ny][nx] each) into the scratch region at
 // diag_fields_offset (uses the whole scratch: 15 doubles per site)
 cudaError_t launch_fields(const DiagLaunch& D, double* fields, cudaStream_t st);
-// The closure network's input in FP32 from post-streaming populations S ([18][n],
-// as handle_pull_Sf writes them): rho_A, rho_B and the physical velocity
-// (j + F/2) / rho, each as (v - mean[c]) / scale[c], into x [4][n]; rho2 [2][n] is
-// scratch for the densities.
-cudaError_t launch_closure_features(const DiagLaunch& D, const float* S, float* rho2, const float mean[4],
+// The closure network's input in FP32: rho_A, rho_B from rho2 [2][n] and the
+// physical velocity (j + F/2) / rho from the momenta j2 [2][n] (the force from the
+// neighbours' densities, as in the diagnostics), each as (v - mean[c]) / scale[c],
+// into x [4][n].
+cudaError_t launch_closure_features(const DiagLaunch& D, const float* rho2, const float* j2, const float mean[4],
                                     const float scale[4], float* x, cudaStream_t st);
-cudaError_t handle_closure_features(lbm_handle* h, const float* S, float* rho2, const float mean[4],
+cudaError_t handle_closure_features(lbm_handle* h, const float* rho2, const float* j2, const float mean[4],
                                     const float scale[4], float* x);
 
 }  // namespace lbm
