@@ -436,15 +436,23 @@ __global__ void __launch_bounds__(256) drho_sum_kernel(const float* __restrict__
                                                        size_t n, float4 oscale, int mode, float2 cbulk,
                                                        double* __restrict__ part) {
     __shared__ double red[2][8];
-    double a = 0.0, b = 0.0;
+    // per thread: compensated FP32 sums (Kahan) of its ~n / (blocks x 256) sites;
+    // FP64 from the warp reduction on (this GPU's FP64 rate is a small fraction of FP32)
+    float sa = 0.0f, ca = 0.0f, sb = 0.0f, cb = 0.0f;
+#pragma unroll 4
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         const float rho[2] = {rho2[k], rho2[n + k]};
         const float w = interface_weight(rho, cbulk);
         float d[2];
         limited_drho(mode, rho, y[k] * oscale.x, y[n + k] * oscale.y, w, d);
-        a += d[0];
-        b += mode == 4 ? w : d[1];
+        const float va = d[0] - ca, ta = sa + va;
+        ca = (ta - sa) - va;
+        sa = ta;
+        const float vb = (mode == 4 ? w : d[1]) - cb, tb = sb + vb;
+        cb = (tb - sb) - vb;
+        sb = tb;
     }
+    double a = (double)sa - (double)ca, b = (double)sb - (double)cb;
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, off);
         b += __shfl_down_sync(0xffffffffu, b, off);
@@ -458,12 +466,36 @@ __global__ void __launch_bounds__(256) drho_sum_kernel(const float* __restrict__
     }
 }
 
-// The block partials summed in a fixed order into part[2 nparts], part[2 nparts + 1].
-__global__ void drho_total_kernel(double* __restrict__ part, int nparts) {
-    if (threadIdx.x < 2) {
-        double v = 0.0;
-        for (int p = 0; p < nparts; ++p) v += part[2 * p + threadIdx.x];
-        part[2 * nparts + threadIdx.x] = v;
+// The block partials summed into part[2 nparts], part[2 nparts + 1] by one block of
+// 256 threads: strided per-thread sums, then a tree in shared memory (fixed order);
+// n sites.
+__global__ void __launch_bounds__(256) drho_total_kernel(double* __restrict__ part, int nparts, size_t n) {
+    __shared__ double red[2][256];
+    double a = 0.0, b = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += 256) {
+        a += part[2 * p];
+        b += part[2 * p + 1];
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // the per-site scalars of correct_kernel, once: sum(h) / sum(w) (mode 4) and
+        // the mean corrections (modes 1-3), as FP32 after part[2 nparts + 1]
+        const double sA = red[0][0], sB = red[1][0];
+        part[2 * nparts] = sA;
+        part[2 * nparts + 1] = sB;
+        float* sc = reinterpret_cast<float*>(part + 2 * nparts + 2);
+        sc[0] = sB > 0.0 ? (float)(sA / sB) : 0.0f;
+        sc[1] = (float)(sA / (double)n);
+        sc[2] = (float)(sB / (double)n);
     }
 }
 
@@ -478,10 +510,10 @@ __global__ void drho_total_kernel(double* __restrict__ part, int nparts) {
 // FP64.
 __global__ void __launch_bounds__(256) correct_kernel(float* __restrict__ S, const float* __restrict__ y, size_t n,
                                                       float4 oscale, int mode, float2 cbulk,
-                                                      const double* __restrict__ total) {
-    const double sA = total[0], sB = total[1];
-    const float hw = mode == 4 && sB > 0.0 ? (float)(sA / sB) : 0.0f;   // mode 4: sum(h) / sum(w)
-    const float mA = (float)(sA / (double)n), mB = (float)(sB / (double)n);
+                                                      const float* __restrict__ scalars) {
+    // mode 4: sum(h) / sum(w); modes 1-3: the mean corrections (from drho_total_kernel)
+    const float hw = mode == 4 ? scalars[0] : 0.0f;
+    const float mA = scalars[1], mB = scalars[2];
     // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
     // full correction of mode 1 feeds back into the growing coarse modes)
     const float du = mode == 1 ? 1.0f : (mode >= 3 ? 0.25f : 0.0f);
@@ -594,10 +626,10 @@ namespace {
 
 float4 f4(const float* a) { return make_float4(a[0], a[1], a[2], a[3]); }
 
-// blocks of the correction's mass sums: 2 partials each + 2 totals fit the
-// 1024-double partial buffer
-constexpr int kCorrBlocks = 480;
-static_assert(2 * kCorrBlocks + 2 <= 1024, "correction partials");
+// blocks of the correction's mass sums (enough for the loads in flight to cover
+// the memory latency): 2 partials each, then 2 totals and 3 FP32 scalars (2 doubles)
+constexpr int kCorrBlocks = 4096;
+constexpr size_t kPartDoubles = 2 * kCorrBlocks + 4;
 
 // restricted fields of the fine run into c->raw (or `dst`)
 lbm_status restrict_fine(lbm_closure* c, float* dst) {
@@ -662,9 +694,11 @@ lbm_status correct(lbm_closure* c, int mode) {
     const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
     lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(rho2, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
-    lbm::drho_total_kernel<<<1, 32, 0, c->stream>>>(c->part, kCorrBlocks);
-    lbm::correct_kernel<<<kCorrBlocks * 4, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,
-                                                                c->part + 2 * kCorrBlocks);
+    lbm::drho_total_kernel<<<1, 256, 0, c->stream>>>(c->part, kCorrBlocks, c->nc);
+    // one site per thread: many blocks keep enough loads in flight
+    const unsigned cblocks = (unsigned)std::min<size_t>((c->nc + 255) / 256, 1u << 30);
+    lbm::correct_kernel<<<cblocks, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,
+                                                       reinterpret_cast<const float*>(c->part + 2 * kCorrBlocks + 2));
     CL_TRY(cudaGetLastError(), "correct");
     CL_TRY(lbm::handle_push_Sf(c->coarse, Sf), "push coarse state");
     return LBM_OK;
@@ -807,7 +841,7 @@ lbm_status lbm_closure_create(const lbm_params* fine, int32_t interval, uint64_t
               cudaMalloc((void**)&c->xin, 4 * c->nc * 4) == cudaSuccess &&
               cudaMalloc((void**)&c->yout, 4 * c->nc * 4) == cudaSuccess &&
               cudaMalloc((void**)&c->S, 18 * c->nc * 8) == cudaSuccess &&
-              cudaMalloc((void**)&c->part, 1024 * 8) == cudaSuccess;
+              cudaMalloc((void**)&c->part, kPartDoubles * 8) == cudaSuccess;
     if (!ok) return bail(LBM_ENOMEM, "closure buffers");
     c->net = lbm::cnn::carve(c->cnn_ws, c->ncx, c->ncy);
     // He-normal weights (Box-Muller on splitmix64), zero biases
