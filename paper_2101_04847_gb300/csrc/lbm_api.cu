@@ -314,9 +314,6 @@ cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, c
     *uy = F + 3 * n;
     return e;
 }
-cudaError_t handle_pull_S(lbm_handle* h, double* S) {
-    return launch_pull_to_double(h->pops(h->cur), h->grid, h->p.storage, h->shift, S, h->stream);
-}
 cudaError_t handle_push_S(lbm_handle* h, const double* S) {
     return launch_push_from_double(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }

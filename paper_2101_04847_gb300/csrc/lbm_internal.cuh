@@ -114,7 +114,6 @@ lbm_status handle_check(lbm_handle* h);
 cudaError_t handle_save_state(lbm_handle* h);
 cudaError_t handle_restore_state(lbm_handle* h);
 cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy);
-cudaError_t handle_pull_S(lbm_handle* h, double* S);
 cudaError_t handle_push_S(lbm_handle* h, const double* S);
 cudaError_t handle_push_Sf(lbm_handle* h, const float* S);   // as handle_push_S, from FP32
 // A handle's current populations as the closure's gather kernel reads them.
