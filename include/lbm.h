@@ -309,7 +309,7 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
  * restoring offset) weighted by 4 c (1 - c) of the normalised mass fraction c, i.e.
  * applied on the interface and not in either bulk.  Corrections keep each component's
  * mass and never halve a density.  Diagnostics of both runs at intervals + 1 times
- * into coarse_out / fine_out (the fine run is the judge and the fallback: if the
+ * into coarse_out / fine_out (the fine run is the reference and the fallback: if the
  * coarse run turns unstable its status is returned, fine_out stays valid). */
 lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out);

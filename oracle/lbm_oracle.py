@@ -23,7 +23,7 @@ One time step (Section 2, "Kinetic equation" and "Equilibrium distribution"):
      bottom wall comes back at its own node as the opposite direction
      (half-way bounce-back, walls at y = -1/2 and y = ny - 1/2).
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * bounce-back variant: half-way (the paper only says "bounce-back");
   * the pseudopotential of a wall node is 0 (no fluid in the solid), and the
     wall indicator S is 1 on the virtual rows y = -1 and y = ny;

@@ -116,7 +116,7 @@ def _errors(co, fi):
 
 
 def test_closure_against_the_coarse_run_without_it(gpu, trained):
-    # held-out seed, 12 intervals (480 fine steps); the fine run is the judge
+    # held-out seed, 12 intervals (480 fine steps); the fine run is the reference
     c, _ = trained
     runs = {mode: c.evaluate(seed=101, warmup=200, intervals=12, use_net=mode) for mode in (0, 2, 3, 4)}
     e = {mode: _errors(*runs[mode]) for mode in runs}
