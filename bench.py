@@ -559,6 +559,45 @@ def run_closure(args):
     print(json.dumps(out), flush=True)
 
 
+def run_closure_accuracy(args):
+    """Accuracy of the learned closure on the fine grid --nx x --ny: the regime of the
+    closure tests (equal pure densities, g = 3e-4, 4-cell perturbation), trained on 6
+    seeded fine runs (8 intervals of 10 coarse steps after 200 fine steps), then the
+    coarse run of 3 held-out seeds over 12 intervals, without correction (0), with the
+    order-parameter correction everywhere (3) and on the interface only (4): relative
+    RMS error of h, E_k, E_p and L_int against the fine run (coarse cells are twice
+    as large; energies per mass scale by 4)."""
+    import numpy as np
+    import torch
+
+    from paper_2101_04847_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    fine = lbm.default_params(nx=args.nx, ny=args.ny, tau_A=1.0, tau_B=1.0, G=1.4, mass_A=1.0, mass_B=1.0,
+                              g=3e-4, n_modes=8, amp=4.0, width=1.5, minority=0.08, crop_rows=10, seed=1)
+    c = lbm.Closure(fine, interval=10, seed=0)
+    t0 = time.time()
+    c.generate(n_runs=6, seed0=11, warmup=200, intervals=8)
+    loss = [c.train(epochs=1, lr=2e-3, shuffle_seed=e) for e in range(25)]
+    train_s = time.time() - t0
+
+    def errors(co, fi):
+        out = {}
+        for k, scale in (("h", 0.5), ("E_k", 4.0), ("E_p", 4.0), ("L_int", 0.5)):
+            f = np.array([d[k] for d in fi]) * scale
+            q = np.array([d[k] for d in co])
+            out[k] = round(float(np.sqrt(np.mean((q - f) ** 2)) / max(np.sqrt(np.mean(f ** 2)), 1e-30)), 4)
+        return out
+
+    res = {}
+    for seed in (101, 102, 103):
+        res[seed] = {mode: errors(*c.evaluate(seed=seed, warmup=200, intervals=12, use_net=mode)) for mode in (0, 3, 4)}
+    c.close()
+    print(json.dumps({"kind": "closure_accuracy", "fine": f"{args.nx}x{args.ny}", "coarse": f"{args.nx // 2}x{args.ny // 2}",
+                      "train": {"loss_first": round(loss[0], 4), "loss_last": round(loss[-1], 4), "seconds": round(train_s, 1)},
+                      "relative_rms_error_vs_fine": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,6 +614,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
     ap.add_argument("--ensemble-grid", dest="ensemble_grid", default="",
                     help="with --ensemble: put every member on this NXxNY grid instead of the drawn ones")
+    ap.add_argument("--closure-accuracy", dest="closure_accuracy", action="store_true",
+                    help="train the closure on the --nx x --ny fine grid and compare held-out coarse runs with the fine run")
     ap.add_argument("--closure", action="store_true",
                     help="time the learned closure (coarse run + correction) against the plain fine solver")
     ap.add_argument("--storage-study", dest="storage_study", type=int, default=0,
@@ -590,6 +631,8 @@ def main():
         run_storage_study(args)
     elif args.closure:
         run_closure(args)
+    elif args.closure_accuracy:
+        run_closure_accuracy(args)
     else:
         run_ours(args)
 
