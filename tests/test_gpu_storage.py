@@ -15,13 +15,16 @@ pytestmark = pytest.mark.gpu
 
 STEPS = 1000
 # max |drho_s| / max |rho_s| after 1000 steps of the 128 x 256 case, per storage.
-# Measured on GB300: f32 3.2e-6, f16 0.0072, bf16 0.013 (the step kernels round
-# the 16-bit stores stochastically with a time-step seeded generator; rounding to
-# nearest gave 0.41 and 0.76, because near-stationary bulk populations rounded the
-# same way every step).
-DENSITY_BOUND = {"f32": 1e-5, "f16": 0.02, "bf16": 0.04}
+# Measured on GB300 (seed 1): f32 3.4e-6, f16 0.0084, bf16 0.038.  The 16-bit
+# errors are interface displacements of a noisy run; against the FP32 run over
+# seeds 1-10 they span f16 0.0074-0.0096 and bf16 0.016-0.038 (median 0.023), and
+# the bounds are twice the largest.  (The step kernels round the 16-bit stores
+# stochastically with a time-step seeded generator; rounding to nearest gave 0.41
+# and 0.76, because near-stationary bulk populations rounded the same way every
+# step.)
+DENSITY_BOUND = {"f32": 1e-5, "f16": 0.02, "bf16": 0.08}
 # relative error of E_p, h, L_int and of the masses after 1000 steps
-# (measured: f16 4.5e-6, 3.7e-3, 0, 1.7e-5; bf16 1.2e-3, 0.145, 0, 1.3e-4).  h sums
+# (measured: f16 8.2e-6, 4.0e-3, 0, 1.7e-6; bf16 1.1e-3, 0.154, 0, 8.7e-5).  h sums
 # c (1 - c) of the row-mean mass fraction over all 236 rows, so the rounding noise
 # of the bulk compositions adds up over the ~220 bulk rows (the oracle's bulk rows
 # already give 0.7 of its 6.0 cells): BF16 moves h by 0.9 cell.
