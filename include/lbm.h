@@ -172,6 +172,16 @@ lbm_status lbm_step_count(lbm_handle* h, int64_t* step);
  * even when the returned status is LBM_EUNSTABLE. */
 lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 
+/* The same evaluation without waiting: lbm_diagnostics_async launches the kernels
+ * and the copies of their results (and of the guard flag) to pinned host memory on
+ * the handle's stream and returns; lbm_diagnostics_wait blocks until those copies
+ * are done (not later work on the stream) and fills *out, with the status
+ * lbm_diagnostics would return.  One evaluation may be pending at a time
+ * (LBM_ESTATE otherwise, and for a wait with none pending).  Lets a caller queue
+ * the next steps before reading this step's result. */
+lbm_status lbm_diagnostics_async(lbm_handle* h);
+lbm_status lbm_diagnostics_wait(lbm_handle* h, lbm_diag* out);
+
 /* Row means of phi = rho_A - rho_B over rows [crop_rows, ny - crop_rows) from
  * the last lbm_diagnostics call: ny - 2 crop_rows doubles written to host_rows. */
 lbm_status lbm_profile(lbm_handle* h, double* host_rows);
@@ -192,6 +202,15 @@ lbm_status lbm_set_populations(lbm_handle* h, const double* host);
  * values are rounded to it as above). */
 lbm_status lbm_get_populations_f32(lbm_handle* h, float* host);
 lbm_status lbm_set_populations_f32(lbm_handle* h, const float* host);
+
+/* Asynchronous form of lbm_set_populations_f32: the host-to-device copy runs on a
+ * copy stream of the handle into a staging buffer (72 bytes per site, allocated on
+ * the first call; LBM_ENOMEM if that fails), so it overlaps work already queued on
+ * the handle's stream; the state is replaced at this point of the handle's stream.
+ * The host buffer must stay unchanged until the copy is done (the next step's
+ * results being read, lbm_sync, or the next call); pinned memory makes the copy
+ * asynchronous. */
+lbm_status lbm_set_populations_f32_async(lbm_handle* h, const float* host);
 
 /* Write the raw stored state (header + populations) to a file / read it back
  * into a handle created with the same nx, ny and storage.  Bitwise round trip. */

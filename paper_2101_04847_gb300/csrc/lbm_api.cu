@@ -148,13 +148,21 @@ struct lbm_handle {
     bool unstable = false;
     bool timed_out = false;
     bool in_ensemble = false;     // stepped by its ensemble only
-    double* host_out = nullptr;   // pinned, kDiagTerms + 2 ny doubles
+    double* host_out = nullptr;   // pinned, kDiagTerms + 2 ny doubles, then the guard flag
     std::vector<double> last_rows;
+    cudaEvent_t ev_diag = nullptr;      // after the last diagnostics' copies to host_out
+    bool diag_pending = false;          // lbm_diagnostics_async issued, not yet collected
+    // asynchronous uploads: a staging buffer filled on a copy stream (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    float* staging = nullptr;
+    cudaEvent_t ev_staged = nullptr, ev_free = nullptr;
+    bool staging_used = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
     void* pops(int k) { return ws + L.pops[k]; }
     double* scratch() { return (double*)(ws + L.scratch); }
     int* flag() { return (int*)(ws + L.flag); }
+    int* host_flag() { return (int*)(host_out + lbm::kDiagTerms + 2 * (size_t)p.ny); }
     // the two time-step counters of the stochastic rounding (after the flag, same region)
     uint32_t* step_ctr() { return (uint32_t*)(ws + L.flag) + 2; }
     uint32_t saved_ctr[2] = {0, 0};   // counters kept with a saved state (tuning)
@@ -521,7 +529,7 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
         }
         h->own_stream = true;
     }
-    cudaError_t e = cudaMallocHost((void**)&h->host_out, (lbm::kDiagTerms + 2 * (size_t)p->ny) * sizeof(double));
+    cudaError_t e = cudaMallocHost((void**)&h->host_out, (lbm::kDiagTerms + 2 * (size_t)p->ny + 1) * sizeof(double));
     if (e != cudaSuccess) {
         h->host_out = nullptr;
         lbm_destroy(h);
@@ -632,16 +640,35 @@ lbm_status lbm_step_count(lbm_handle* h, int64_t* step) {
     return LBM_OK;
 }
 
-lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
-    if (!h || !out) return fail(LBM_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// The diagnostics kernels, their results and the guard flag copied to the pinned
+// host buffer, and an event after them; nothing waits.
+lbm_status diag_issue(lbm_handle* h) {
     const lbm_params& p = h->p;
     lbm::DiagLaunch D = diag_launch(h);
     LBM_TRY(lbm::launch_diagnostics(D, h->stream), "diagnostics kernels");
     const int nrows = p.ny - 2 * p.crop_rows;
     LBM_TRY(cudaMemcpyAsync(h->host_out, D.out, (lbm::kDiagTerms + 2 * (size_t)nrows) * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream), "copy diagnostics");
-    lbm_status st = check_flag(h);  // synchronises the stream
-    if (st != LBM_OK && st != LBM_EUNSTABLE) return st;
+    LBM_TRY(cudaMemcpyAsync(h->host_flag(), h->flag(), sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flag");
+    if (!h->ev_diag) LBM_TRY(cudaEventCreateWithFlags(&h->ev_diag, cudaEventDisableTiming), "diagnostics event");
+    LBM_TRY(cudaEventRecord(h->ev_diag, h->stream), "record diagnostics event");
+    return LBM_OK;
+}
+
+// Waits for the event of diag_issue (not for later work on the stream) and fills *out.
+lbm_status diag_collect(lbm_handle* h, lbm_diag* out) {
+    LBM_TRY(cudaEventSynchronize(h->ev_diag), "wait for diagnostics");
+    const int flag = *h->host_flag();
+    if (flag & 1) h->unstable = true;
+    if (flag & 2) h->timed_out = true;
+    if (h->timed_out) return fail(LBM_ETIMEOUT, "a bounded wait for a staged row copy gave up");
+    const lbm_status st = h->unstable ? fail(LBM_EUNSTABLE, "NaN or negative density seen by the step") : LBM_OK;
+    const lbm_params& p = h->p;
+    const int nrows = p.ny - 2 * p.crop_rows;
     const double* o = h->host_out;
     const double Dn = (double)p.nx * nrows;
     const double cs2 = 1.0 / 3.0;
@@ -679,6 +706,33 @@ lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
     out->h = 6.0 * hw;
     out->status = h->unstable ? LBM_EUNSTABLE : LBM_OK;
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
+    if (!h || !out) return fail(LBM_EINVAL, "NULL argument");
+    if (h->diag_pending) return fail(LBM_ESTATE, "collect the pending lbm_diagnostics_async first");
+    lbm_status st = diag_issue(h);
+    if (st != LBM_OK) return st;
+    return diag_collect(h, out);
+}
+
+lbm_status lbm_diagnostics_async(lbm_handle* h) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (h->diag_pending) return fail(LBM_ESTATE, "collect the pending lbm_diagnostics_async first");
+    lbm_status st = diag_issue(h);
+    if (st == LBM_OK) h->diag_pending = true;
+    return st;
+}
+
+lbm_status lbm_diagnostics_wait(lbm_handle* h, lbm_diag* out) {
+    if (!h || !out) return fail(LBM_EINVAL, "NULL argument");
+    if (!h->diag_pending) return fail(LBM_ESTATE, "no lbm_diagnostics_async pending");
+    h->diag_pending = false;
+    return diag_collect(h, out);
 }
 
 lbm_status lbm_profile(lbm_handle* h, double* host_rows) {
@@ -730,6 +784,33 @@ lbm_status lbm_get_populations_f32(lbm_handle* h, float* host) {
     const size_t n = (size_t)18 * h->p.nx * h->p.ny;
     LBM_TRY(cudaMemcpyAsync(host, S, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "copy populations");
     LBM_TRY(cudaStreamSynchronize(h->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations_f32_async(lbm_handle* h, const float* host) {
+    if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+    const size_t n = (size_t)18 * h->p.nx * h->p.ny;
+    if (!h->staging) {
+        LBM_TRY(cudaSetDevice(h->device), "set device");
+        if (cudaMalloc((void**)&h->staging, n * sizeof(float)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->staging = nullptr;
+            return fail(LBM_ENOMEM, "staging buffer of the asynchronous upload");
+        }
+        LBM_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+        LBM_TRY(cudaEventCreateWithFlags(&h->ev_staged, cudaEventDisableTiming), "upload event");
+        LBM_TRY(cudaEventCreateWithFlags(&h->ev_free, cudaEventDisableTiming), "upload event");
+    }
+    // the previous upload's push has read the staging buffer before it is refilled
+    if (h->staging_used) LBM_TRY(cudaStreamWaitEvent(h->copy_stream, h->ev_free, 0), "wait for staging");
+    LBM_TRY(cudaMemcpyAsync(h->staging, host, n * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream),
+            "copy populations");
+    LBM_TRY(cudaEventRecord(h->ev_staged, h->copy_stream), "record upload");
+    LBM_TRY(cudaStreamWaitEvent(h->stream, h->ev_staged, 0), "order upload");
+    LBM_TRY(lbm::launch_push_from_float(h->staging, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream),
+            "push kernel");
+    LBM_TRY(cudaEventRecord(h->ev_free, h->stream), "record push");
+    h->staging_used = true;
     return LBM_OK;
 }
 
@@ -807,7 +888,13 @@ void lbm_destroy(lbm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->host_out) cudaFreeHost(h->host_out);
+    if (h->ev_diag) cudaEventDestroy(h->ev_diag);
+    if (h->ev_staged) cudaEventDestroy(h->ev_staged);
+    if (h->ev_free) cudaEventDestroy(h->ev_free);
+    if (h->staging) cudaFree(h->staging);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -61,12 +61,15 @@ _PROTOS = {
     "lbm_sync": (C.c_int, [_h]),
     "lbm_step_count": (C.c_int, [_h, _P(C.c_int64)]),
     "lbm_diagnostics": (C.c_int, [_h, _P(LbmDiag)]),
+    "lbm_diagnostics_async": (C.c_int, [_h]),
+    "lbm_diagnostics_wait": (C.c_int, [_h, _P(LbmDiag)]),
     "lbm_profile": (C.c_int, [_h, _dp]),
     "lbm_get_fields": (C.c_int, [_h, _dp, _dp, _dp, _dp]),
     "lbm_get_populations": (C.c_int, [_h, _dp]),
     "lbm_set_populations": (C.c_int, [_h, _dp]),
     "lbm_get_populations_f32": (C.c_int, [_h, C.c_void_p]),
     "lbm_set_populations_f32": (C.c_int, [_h, C.c_void_p]),
+    "lbm_set_populations_f32_async": (C.c_int, [_h, C.c_void_p]),
     "lbm_save": (C.c_int, [_h, C.c_char_p]),
     "lbm_load": (C.c_int, [_h, C.c_char_p]),
     "lbm_destroy": (None, [_h]),
@@ -240,6 +243,25 @@ class Solver:
         if check or st not in (LBM_OK, LBM_EUNSTABLE):
             _check(st, "lbm_diagnostics")
         return diag_dict(d)
+
+    def diagnostics_async(self):
+        """Queue a diagnostics evaluation; diagnostics_wait() collects it."""
+        _check(self.lib.lbm_diagnostics_async(self._h), "lbm_diagnostics_async")
+
+    def diagnostics_wait(self, check: bool = True) -> dict:
+        d = LbmDiag()
+        st = self.lib.lbm_diagnostics_wait(self._h, C.byref(d))
+        if check or st not in (LBM_OK, LBM_EUNSTABLE):
+            _check(st, "lbm_diagnostics_wait")
+        return diag_dict(d)
+
+    def set_populations_async(self, f: np.ndarray):
+        """Replace the state from a float32 host array without waiting for the copy
+        (pinned memory overlaps it with the work already queued); `f` must stay
+        unchanged until the copy is done."""
+        if f.dtype != np.float32 or not f.flags.c_contiguous or f.shape != (2, 9, self.ny, self.nx):
+            raise ValueError(f"populations must be a C-contiguous float32 array of shape (2, 9, {self.ny}, {self.nx})")
+        _check(self.lib.lbm_set_populations_f32_async(self._h, f.ctypes.data), "lbm_set_populations_f32_async")
 
     def profile(self) -> np.ndarray:
         rows = np.empty(self.ny - 2 * self.params.crop_rows)

@@ -125,3 +125,57 @@ def test_fp32_population_transfer_matches_the_fp64_one(gpu, storage):
         ga, gb = a.populations(), b.populations(out=np.empty(f.shape, dtype=np.float32))
         assert gb.dtype == np.float32
         assert np.array_equal(ga, gb.astype(np.float64))
+
+
+def test_async_upload_and_diagnostics_equal_the_synchronous_calls(gpu):
+    # the same upload, steps and evaluation through the asynchronous entry points,
+    # pipelined as the end-to-end bench runs them, give bitwise the same results
+    import torch
+
+    d = inputs.params(inputs.C0, nx=160, ny=96, crop_rows=4)
+    host = torch.empty((2, 9, 96, 160), dtype=torch.float32, pin_memory=True).numpy()
+    with lbm.Solver(**d) as s:
+        s.step(30)
+        s.populations(out=host)
+        ref = []
+        for _ in range(3):
+            s.set_populations(host)
+            s.step(20)
+            ref.append(s.diagnostics())
+        f_ref = s.populations()
+    with lbm.Solver(**d) as s:
+        got = []
+        s.set_populations_async(host)
+        s.step(20)
+        s.diagnostics_async()
+        for _ in range(2):
+            s.set_populations_async(host)
+            s.step(20)
+            got.append(s.diagnostics_wait())
+            s.diagnostics_async()
+        got.append(s.diagnostics_wait())
+        f_got = s.populations()
+        with pytest.raises(lbm.LbmError) as e:
+            s.diagnostics_wait()                      # nothing pending
+        assert e.value.status == lbm.LBM_ESTATE
+        s.diagnostics_async()
+        with pytest.raises(lbm.LbmError):
+            s.diagnostics_async()                     # one pending at a time
+        s.diagnostics_wait()
+    assert np.array_equal(f_got, f_ref)
+    for a, b in zip(got, ref):
+        for k in ("E_k", "E_p", "h", "L_int", "mass_A", "mass_B", "viscous", "enstrophy"):
+            assert a[k] == b[k], k
+
+
+def test_async_diagnostics_report_an_unstable_state(gpu):
+    d = inputs.params(inputs.C0, nx=64, ny=32, crop_rows=4)
+    with lbm.Solver(**d) as s:
+        f = s.populations().astype(np.float32)
+        f[0, 0, 10, 10] = np.nan
+        s.set_populations_async(np.ascontiguousarray(f))
+        s.step(3)
+        s.diagnostics_async()
+        with pytest.raises(lbm.LbmError) as e:
+            s.diagnostics_wait()
+        assert e.value.status == lbm.LBM_EUNSTABLE
