@@ -323,7 +323,7 @@ def run_ensemble(args):
     if args.ensemble_grid:   # every member on one grid (e.g. small grids that cannot fill the GPU alone)
         nx, ny = (int(v) for v in args.ensemble_grid.lower().split("x"))
         members = [dict(m, nx=nx, ny=ny) for m in members]
-    lb_steps = 20
+    lb_steps = 50   # one captured 50-step graph per bench step
     params = [lbm.default_params(kernel="staged", **m) for m in members]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
