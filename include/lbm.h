@@ -183,7 +183,8 @@ lbm_status lbm_diagnostics_async(lbm_handle* h);
 lbm_status lbm_diagnostics_wait(lbm_handle* h, lbm_diag* out);
 
 /* Row means of phi = rho_A - rho_B over rows [crop_rows, ny - crop_rows) from
- * the last lbm_diagnostics call: ny - 2 crop_rows doubles written to host_rows. */
+ * the last evaluation read (lbm_diagnostics or lbm_diagnostics_wait):
+ * ny - 2 crop_rows doubles written to host_rows. */
 lbm_status lbm_profile(lbm_handle* h, double* host_rows);
 
 /* rho_A, rho_B and the physical velocity components on the whole grid, nx*ny
@@ -207,9 +208,9 @@ lbm_status lbm_set_populations_f32(lbm_handle* h, const float* host);
  * copy stream of the handle into a staging buffer (72 bytes per site, allocated on
  * the first call; LBM_ENOMEM if that fails), so it overlaps work already queued on
  * the handle's stream; the state is replaced at this point of the handle's stream.
- * The host buffer must stay unchanged until the copy is done (the next step's
- * results being read, lbm_sync, or the next call); pinned memory makes the copy
- * asynchronous. */
+ * The host buffer must stay unchanged until the copy is done: lbm_sync returns,
+ * or a result queued after this call is read (lbm_diagnostics_wait, or any
+ * synchronising call); pinned memory makes the copy asynchronous. */
 lbm_status lbm_set_populations_f32_async(lbm_handle* h, const float* host);
 
 /* Write the raw stored state (header + populations) to a file / read it back

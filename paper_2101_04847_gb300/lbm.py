@@ -258,7 +258,7 @@ class Solver:
     def set_populations_async(self, f: np.ndarray):
         """Replace the state from a float32 host array without waiting for the copy
         (pinned memory overlaps it with the work already queued); `f` must stay
-        unchanged until the copy is done."""
+        unchanged until sync() returns or a result queued after this call is read."""
         if f.dtype != np.float32 or not f.flags.c_contiguous or f.shape != (2, 9, self.ny, self.nx):
             raise ValueError(f"populations must be a C-contiguous float32 array of shape (2, 9, {self.ny}, {self.nx})")
         _check(self.lib.lbm_set_populations_f32_async(self._h, f.ctypes.data), "lbm_set_populations_f32_async")
