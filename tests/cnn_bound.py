@@ -4,8 +4,9 @@ with the same BF16 weights.  A catch-all (it sums |w| |a| over 288 terms per
 layer, so it is ~100 times the typical error); the tight comparison is with
 the oracle's forward_bf16_activations.
 
-Rounding to BF16 (nearest) moves a value v by at most u |v|, u = 2^-9; an FP32
-sum of K products errs by at most K 2^-24 times the sum of their magnitudes.
+Rounding to BF16 (nearest; 8 significant bits) moves a value v by at most u |v|,
+u = 2^-8; an FP32 sum of K products errs by at most K 2^-24 times the sum of their
+magnitudes.
 Both propagate through a convolution as through the convolution with |w|, and
 through ReLU without growth (it is 1-Lipschitz).  With e the bound on a layer's
 input error and a its exact value:
@@ -20,7 +21,7 @@ import torch
 
 from oracle import cnn_oracle as N
 
-U_BF16 = 2.0 ** -9
+U_BF16 = 2.0 ** -8
 EPS_F32 = 2.0 ** -24
 
 

@@ -76,6 +76,18 @@ def test_bf16_activation_forward_against_the_exact_network():
         assert np.mean(np.abs(bad - y) > 1e-5 * np.max(np.abs(y))) > 0.5, mistake
 
 
+def test_bf16_unit_roundoff_of_the_bound():
+    # the bound's unit roundoff covers every relative rounding error of round_bf16
+    # and is not loose by a factor 2: 8 significant bits round to within 2^-8, and
+    # values just below a tie come close to it
+    from tests.cnn_bound import U_BF16
+
+    v = np.random.default_rng(9).uniform(-300.0, 300.0, 200000)
+    rel = np.abs(N.round_bf16(torch.tensor(v)).numpy() - v) / np.abs(v)
+    assert rel.max() <= U_BF16
+    assert rel.max() > 0.75 * U_BF16
+
+
 def test_round_bf16_against_hand_values():
     # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: to even (1); 1 + 3 * 2^-8 rounds up
     # to 1 + 2^-6 (even); 2^-7 spacing at 1; values already BF16 stay
