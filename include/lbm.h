@@ -337,9 +337,33 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
 /* Production use of the closure: advance the coarse run by `intervals` intervals
  * of `interval` coarse steps, correcting it after each with mode use_net (0 = no
  * correction, 1-4 as in lbm_closure_evaluate), without running the fine solver.
- * Needs trained (or set) parameters for use_net > 0 (else LBM_ESTATE).
- * Asynchronous on the closure's stream except where a correction reads back. */
+ * Needs trained (or set) parameters for use_net > 0 (else LBM_ESTATE).  Queued on
+ * the closure's stream; with use_net > 0 it then synchronises once to read the
+ * tensor-core kernels' status: LBM_ETIMEOUT if a bounded wait of theirs gave up in
+ * any interval (the coarse state is then unreliable).
+ *
+ * One correction, per site of the coarse grid (f the populations after streaming,
+ * rho_s = sum_i f_i^s, rho = rho_A + rho_B, u_b = sum_{s,i} f_i^s c_i / rho):
+ *   network input x = ((rho_A, rho_B, u_x, u_y) - in_mean) / in_scale with u the
+ *     physical velocity (sum_{s,i} f_i^s c_i + F / 2) / rho, F the total force;
+ *   p = CNN(x) * out_scale (lbm_cnn_infer), p = (dA, dB, du_x, du_y);
+ *   d_s: mode 1 max(p_s, -rho_s / 2) minus its grid mean; modes 2, 3
+ *     h = clamp((dA - dB) / 2, -rho_A / 2, rho_B / 2), d_A = h - mean(h), d_B = -d_A;
+ *     mode 4 h = clamp(w (dA - dB) / 2, ...) with w = 4 c (1 - c), c the mass fraction
+ *     rho_A / rho normalised by its bulk values (lbm_closure_evaluate) and clamped to
+ *     [0, 1], d_A = h - w sum(h) / sum(w), d_B = -d_A;
+ *   u' = u_b + a du, a = 1 (mode 1), 0 (mode 2), 1/4 (modes 3, 4);
+ *   rho'_s = max(rho_s + d_s, 0),
+ *   f_i^s <- f_i^eq(rho'_s, u') + (rho'_s / rho_s) (f_i^s - f_i^eq(rho_s, u_b)).
+ * Arithmetic in FP32 per site, the grid sums in FP64. */
 lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_net);
+
+/* One correction (mode use_net, as above) of the coarse run's current state, with
+ * no time steps: lbm_closure_advance is lbm_step(coarse, interval) followed by this
+ * call, interval after interval.  use_net 0 does nothing.  LBM_ESTATE without
+ * trained or set parameters; synchronises the closure's stream and returns
+ * LBM_ETIMEOUT as lbm_closure_advance does. */
+lbm_status lbm_closure_correct(lbm_closure* c, int32_t use_net);
 
 /* Copy the network parameters to (set = 0) or from (set = 1) host memory. */
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set);
@@ -349,6 +373,11 @@ lbm_status lbm_closure_solvers(lbm_closure* c, lbm_handle** fine, lbm_handle** c
 
 /* Input means, input scales and output scales (12 floats) used by the network. */
 lbm_status lbm_closure_normalisation(lbm_closure* c, float* host12);
+
+/* Set them (host12 as above), e.g. with parameters saved from an earlier training:
+ * LBM_EINVAL unless all 12 are finite and the 8 scales positive;
+ * lbm_closure_train overwrites them with the statistics of its samples. */
+lbm_status lbm_closure_set_normalisation(lbm_closure* c, const float* host12);
 
 void lbm_closure_destroy(lbm_closure* c);
 

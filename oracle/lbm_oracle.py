@@ -32,8 +32,9 @@ Readings of points the paper leaves open:
   * diagnostic velocity: u_phys = (sum_{s,i} f c + F/2) / rho;
   * the garbled |grad phi^2| in the Korteweg tensor is read as |grad phi|^2;
   * eta = rho_bar * c_s^2 (tau - 1/2), rho_bar = mean density of the sub-domain;
-  * mixing-layer width h = 6 sum_y cbar (1 - cbar) on the normalised row-mean
-    order parameter (the definition lives in a companion paper we do not have);
+  * mixing-layer width h = 6 sum_y cbar (1 - cbar) on the normalised row mean of
+    the mass fraction rho_A / (rho_A + rho_B) (the definition lives in a companion
+    paper we do not have);
   * interface length: 4-direction Cauchy-Crofton estimate, phi > 0 is "A".
 
 Pins: tests/test_oracle_*.py check this module against closed forms,

@@ -678,7 +678,10 @@ cudaError_t launch_closure_pull(const lbm::PopView& v, float* S, float* rho2, fl
     return cudaGetLastError();
 }
 
-lbm_status correct(lbm_closure* c, int mode) {
+// clear_status: start the tensor-core kernels' status word from 0 (the first
+// correction of a call); later ones keep an earlier failure raised for the check
+// at the end of the call
+lbm_status correct(lbm_closure* c, int mode, bool clear_status) {
     // bulk mass fractions of the coarse run's initial state (pure A on top, pure B below)
     const lbm_params& q = c->coarse_p;
     const double2 cbulk = make_double2(q.mass_A / (q.mass_A + q.minority * q.mass_B),
@@ -690,7 +693,7 @@ lbm_status correct(lbm_closure* c, int mode) {
     float* j2 = c->raw + 2 * c->nc;
     CL_TRY(launch_closure_pull(lbm::handle_pops(c->coarse), Sf, rho2, j2), "pull coarse state");
     CL_TRY(lbm::handle_closure_features(c->coarse, rho2, j2, c->in_mean, c->in_scale, c->xin), "network input");
-    CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream), "cnn inference");
+    CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream, false, clear_status), "cnn inference");
     const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
     lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(rho2, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
@@ -701,6 +704,17 @@ lbm_status correct(lbm_closure* c, int mode) {
                                                        reinterpret_cast<const float*>(c->part + 2 * kCorrBlocks + 2));
     CL_TRY(cudaGetLastError(), "correct");
     CL_TRY(lbm::handle_push_Sf(c->coarse, Sf), "push coarse state");
+    return LBM_OK;
+}
+
+// Synchronises the closure's stream and reads the tensor-core kernels' status word:
+// LBM_ETIMEOUT if one of their waits gave up since the word was last cleared.
+lbm_status cnn_check(lbm_closure* c) {
+    int st = 0;
+    CL_TRY(lbm::cnn_tc::status(c->net.tc, c->stream, &st), "cnn inference status");
+    if (st != 0)
+        return cl_fail(LBM_ETIMEOUT, "a wait of the tensor-core CNN kernels gave up (status " + std::to_string(st) +
+                                         "): the corrected state is unreliable");
     return LBM_OK;
 }
 
@@ -976,17 +990,13 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
     CL_STATUS(lbm_diagnostics(c->fine, &fine_out[0]));
     for (int k = 1; k <= intervals; ++k) {
         CL_STATUS(lbm_step(c->coarse, c->interval));
-        if (use_net) CL_STATUS(correct(c, use_net));
+        if (use_net) CL_STATUS(correct(c, use_net, k == 1));
         CL_STATUS(lbm_step(c->fine, kFineStepsPerCoarse * c->interval));
         lbm_status st = lbm_diagnostics(c->coarse, &coarse_out[k]);
         if (st != LBM_OK) return st;   // the caller falls back to the fine run (fine_out stays valid)
         CL_STATUS(lbm_diagnostics(c->fine, &fine_out[k]));
     }
-    if (use_net) {
-        int st = 0;
-        CL_TRY(lbm::cnn_tc::status(c->net.tc, c->stream, &st), "cnn inference status");
-        if (st != 0) return cl_fail(LBM_ETIMEOUT, "a wait of the tensor-core CNN kernels gave up");
-    }
+    if (use_net && intervals > 0) CL_STATUS(cnn_check(c));
     return LBM_OK;
 }
 
@@ -996,9 +1006,19 @@ lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_ne
     if (use_net && !c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
     for (int k = 0; k < intervals; ++k) {
         CL_STATUS(lbm_step(c->coarse, c->interval));
-        if (use_net) CL_STATUS(correct(c, use_net));
+        if (use_net) CL_STATUS(correct(c, use_net, k == 0));
     }
+    if (use_net && intervals > 0) CL_STATUS(cnn_check(c));
     return LBM_OK;
+}
+
+lbm_status lbm_closure_correct(lbm_closure* c, int32_t use_net) {
+    if (!c) return cl_fail(LBM_EINVAL, "NULL closure");
+    if (use_net < 0 || use_net > 4) return cl_fail(LBM_EINVAL, "use_net must be 0 to 4");
+    if (use_net == 0) return LBM_OK;
+    if (!c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
+    CL_STATUS(correct(c, use_net, true));
+    return cnn_check(c);
 }
 
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set) {
@@ -1025,6 +1045,19 @@ lbm_status lbm_closure_normalisation(lbm_closure* c, float* host12) {
         host12[i] = c->in_mean[i];
         host12[4 + i] = c->in_scale[i];
         host12[8 + i] = c->out_scale[i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_set_normalisation(lbm_closure* c, const float* host12) {
+    if (!c || !host12) return cl_fail(LBM_EINVAL, "NULL argument");
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(host12[i]) || (i >= 4 && !(host12[i] > 0.0f)))
+            return cl_fail(LBM_EINVAL, "normalisation: values must be finite and the scales positive");
+    for (int i = 0; i < 4; ++i) {
+        c->in_mean[i] = host12[i];
+        c->in_scale[i] = host12[4 + i];
+        c->out_scale[i] = host12[8 + i];
     }
     return LBM_OK;
 }

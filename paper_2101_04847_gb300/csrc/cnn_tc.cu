@@ -385,12 +385,12 @@ __global__ void weights_kernel(const float* __restrict__ w, int cin, int cout, i
 }
 
 // Input planes (4 channels + 4 zeros, ghost columns, zero wall rows), the wall
-// rows of the hidden planes, and the status word.
+// rows of the hidden planes, and (clear != 0) the status word.
 __global__ void prep_kernel(const float* __restrict__ x, int nx, int ny, int pitch, uint8_t* __restrict__ xin,
-                            uint8_t* __restrict__ h1, uint8_t* __restrict__ h2, int* __restrict__ status) {
+                            uint8_t* __restrict__ h1, uint8_t* __restrict__ h2, int* __restrict__ status, int clear) {
     const size_t n = (size_t)nx * ny;
     const size_t total = (size_t)(ny + 2) * pitch;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+    if (clear && blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / pitch), p = (int)(i % pitch);
         uint4 val = make_uint4(0u, 0u, 0u, 0u);
@@ -483,14 +483,16 @@ Bufs carve(void* base, int nx, int ny) {
     return B;
 }
 
-cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st, bool withhold) {
+cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st, bool withhold,
+                  bool clear_status) {
     const int wh = withhold ? 1 : 0;
     weights_kernel<<<8, 256, 0, st>>>(params + kW1, kIn, kHid, 1, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w1));
     weights_kernel<<<16, 256, 0, st>>>(params + kW2, kHid, kHid, 2, kHid, nfold(kHid), reinterpret_cast<__nv_bfloat16*>(B.w2));
     weights_kernel<<<4, 256, 0, st>>>(params + kW3, kHid, kOut, 2, kOut, nfold(kOut), reinterpret_cast<__nv_bfloat16*>(B.w3));
     const size_t px = (size_t)(B.ny + 2) * B.pitch;
     const int blocks = (int)std::min<size_t>(4096, (px + 255) / 256);
-    prep_kernel<<<blocks, 256, 0, st>>>(x, B.nx, B.ny, B.pitch, B.xin, B.h1, B.h2, B.status);
+    prep_kernel<<<blocks, 256, 0, st>>>(x, B.nx, B.ny, B.pitch, B.xin, B.h1, B.h2, B.status,
+                                                clear_status ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_conv<1, 2, 32, true>(B, B.xin, B.w1, params + kB1, B.h1, nullptr, st, wh);

@@ -31,9 +31,10 @@ size_t bytes(int nx, int ny);
 Bufs carve(void* base, int nx, int ny);
 // y[4][ny][nx] = CNN(x[4][ny][nx]); params as in the FP32 path.  Asynchronous.
 // withhold (tests of the timeout path only): the kernels issue no copies and poll
-// briefly, so their waits give up and raise the status word.
+// briefly, so their waits give up and raise the status word.  clear_status: the
+// status word starts from 0; without it a failure of an earlier call stays raised.
 cudaError_t infer(const Bufs& B, const float* params, const float* x, float* y, cudaStream_t st,
-                  bool withhold = false);
+                  bool withhold = false, bool clear_status = true);
 // Reads the status word (synchronises the stream): 0 if every wait completed.
 cudaError_t status(const Bufs& B, cudaStream_t st, int* out);
 

@@ -101,6 +101,8 @@ _PROTOS = {
                                        _P(LbmDiag)]),
     "lbm_closure_params": (C.c_int, [C.c_void_p, _P(C.c_float), C.c_int32]),
     "lbm_closure_normalisation": (C.c_int, [C.c_void_p, _P(C.c_float)]),
+    "lbm_closure_set_normalisation": (C.c_int, [C.c_void_p, _P(C.c_float)]),
+    "lbm_closure_correct": (C.c_int, [C.c_void_p, C.c_int32]),
     "lbm_closure_solvers": (C.c_int, [C.c_void_p, _P(_h), _P(_h)]),
     "lbm_closure_destroy": (None, [C.c_void_p]),
 }
@@ -470,6 +472,10 @@ class Closure:
         """Advance the coarse run by `intervals` corrected intervals (no fine run)."""
         _check(self.lib.lbm_closure_advance(self._c, int(intervals), int(use_net)), "lbm_closure_advance")
 
+    def correct(self, use_net: int):
+        """One correction of the coarse run's current state (no time steps)."""
+        _check(self.lib.lbm_closure_correct(self._c, int(use_net)), "lbm_closure_correct")
+
     def params(self) -> np.ndarray:
         out = np.empty(CNN_PARAMS, dtype=np.float32)
         _check(self.lib.lbm_closure_params(self._c, out.ctypes.data_as(_P(C.c_float)), 0), "lbm_closure_params")
@@ -489,6 +495,13 @@ class Closure:
         out = np.empty(12, dtype=np.float32)
         _check(self.lib.lbm_closure_normalisation(self._c, out.ctypes.data_as(_P(C.c_float))), "lbm_closure_normalisation")
         return out
+
+    def set_normalisation(self, in_mean, in_scale, out_scale):
+        v = np.ascontiguousarray(np.concatenate([in_mean, in_scale, out_scale]), dtype=np.float32)
+        if v.size != 12:
+            raise ValueError("normalisation: 4 input means, 4 input scales, 4 output scales")
+        _check(self.lib.lbm_closure_set_normalisation(self._c, v.ctypes.data_as(_P(C.c_float))),
+               "lbm_closure_set_normalisation")
 
     def close(self):
         if getattr(self, "_c", None) and self._c.value:

@@ -5,7 +5,9 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle import closure_oracle as K
 from oracle import cnn_oracle as N
+from oracle import lbm_oracle as O
 from paper_2101_04847_gb300 import lbm
 from tests import inputs
 
@@ -163,4 +165,125 @@ def test_advance_runs_the_corrected_coarse_solver_alone(gpu, trained):
     fresh.advance(1, 0)
     with pytest.raises(lbm.LbmError):
         fresh.advance(1, 5)
+    with pytest.raises(lbm.LbmError):
+        fresh.correct(4)                         # no trained or set parameters
+    fresh.correct(0)
+    with pytest.raises(lbm.LbmError):
+        fresh.correct(5)
     fresh.close()
+
+
+def coarse_oracle_params(c):
+    d = lbm.params_dict(c.coarse)
+    d = {k: v for k, v in d.items() if k in O.Params.__dataclass_fields__}
+    if d["y0"] < 0:
+        d["y0"] = None
+    return O.Params(**d)
+
+
+def seeded_correction_inputs(c):
+    """Seeded inputs of one correction: the coarse state from the oracle (60 coarse
+    steps of the coarsened workload, rounded to FP32), He-initialised parameters
+    with a random output bias, and a normalisation from the state's statistics."""
+    pc = coarse_oracle_params(c)
+    f0 = inputs.as_float32(O.step(O.initial_populations(pc), pc, 60))
+    rng = np.random.default_rng(23)
+    p = N.init_params(23)
+    p[-4:] = rng.normal(0.0, 0.3, 4)
+    raw = K.network_input(f0, pc, np.zeros(4), np.ones(4))
+    norm = (raw.mean(axis=(1, 2)).astype(np.float32), raw.std(axis=(1, 2)).astype(np.float32),
+            np.array([3e-3, 3e-3, 4e-3, 4e-3], dtype=np.float32))
+    return pc, f0, p.astype(np.float32), norm
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
+def test_one_correction_matches_the_oracle(gpu, mode):
+    # the correction alone (lbm_closure_correct) on a state both sides hold exactly:
+    # the network input in FP32 from the same populations differs from the oracle's
+    # by rounding only, so BF16 rounding decisions agree (but for rare ties); the
+    # oracle evaluates the network with BF16 activations, as the tensor cores do,
+    # and applies the correction in FP64
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        pc, f0, p32, (in_mean, in_scale, out_scale) = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(in_mean, in_scale, out_scale)
+        _, co = c.solvers()
+        co.set_populations(f0.astype(np.float32))
+        c.correct(mode)
+        f_gpu = co.populations()
+    finally:
+        c.close()
+    x = K.network_input(f0, pc, in_mean.astype(np.float64), in_scale.astype(np.float64))
+    y = N.forward_bf16_activations(oracle_view(p32), x)["y"].numpy()
+    f_ref = K.correct(f0, y, out_scale.astype(np.float64), mode, pc)
+    d_gpu, d_ref = f_gpu - f0, f_ref - f0
+    big = np.max(np.abs(d_ref))
+    err = np.abs(d_gpu - d_ref)
+    off = float(np.mean(err > 1e-4 * big))
+    print(f"\nmode {mode}: largest increment {big:.3e}; error max {err.max() / big:.2e}, "
+          f"median {np.median(err) / big:.2e} of it; {off:.2%} of the values beyond 1e-4 of it")
+    assert big > 1e-3
+    # FP32 arithmetic on populations up to 0.58 (a few 1e-8 absolute) is ~2e-5 of
+    # the largest increment, the mass-restoring offset an FP64 sum on both sides
+    assert np.median(err) <= 1e-5 * big
+    # where a stored input or activation rounds to the other BF16 neighbour in the two
+    # evaluations (its FP32 and FP64 values straddle a rounding boundary), a 3 x 3 to
+    # 5 x 5 patch of outputs moves, each by well under 1 % of the largest increment
+    # (measured, modes 1-4: median 0.8-2.9e-7, 0.4-0.9 % of the values beyond 1e-4,
+    # the largest 1.7-4.4e-3 of the largest increment)
+    assert off <= 0.05
+    assert err.max() <= 1e-2 * big
+    m0 = O.densities(f0).sum(axis=(1, 2))
+    m1 = O.densities(f_gpu).sum(axis=(1, 2))
+    assert np.allclose(m1, m0, rtol=1e-6)
+
+
+def test_advance_is_the_steps_then_the_correction(gpu):
+    # lbm_closure_advance(1, 4) from a state equals lbm_step(interval) followed by
+    # lbm_closure_correct(4), bit for bit; and against the oracle (its own 10 FP64
+    # steps, then the correction) the advanced state agrees to the FP32 steps'
+    # rounding plus the BF16 rounding decisions that this rounding moves
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        pc, f0, p32, (in_mean, in_scale, out_scale) = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(in_mean, in_scale, out_scale)
+        _, co = c.solvers()
+        co.set_populations(f0.astype(np.float32))
+        c.advance(1, 4)
+        a = co.populations()
+        co.set_populations(f0.astype(np.float32))
+        c.advance(1, 0)
+        plain = co.populations()
+        c.correct(4)
+        b = co.populations()
+    finally:
+        c.close()
+    assert np.array_equal(a, b)
+    f10 = O.step(f0, pc, 10)
+    x = K.network_input(f10, pc, in_mean.astype(np.float64), in_scale.astype(np.float64))
+    y = N.forward_bf16_activations(oracle_view(p32), x)["y"].numpy()
+    f_ref = K.correct(f10, y, out_scale.astype(np.float64), 4, pc)
+    d_gpu, d_ref = a - plain, f_ref - f10
+    rms = np.sqrt(np.mean((d_gpu - d_ref) ** 2)) / np.sqrt(np.mean(d_ref ** 2))
+    print(f"\nadvance: state error {np.max(np.abs(plain - f10)):.2e} before the correction, "
+          f"{np.max(np.abs(a - f_ref)):.2e} after; relative RMS error of the correction {rms:.2e}")
+    # (measured: 1.9e-7 before the correction, relative RMS 5.6e-4)
+    assert np.max(np.abs(plain - f10)) <= 1e-5 * np.max(np.abs(f10))
+    assert rms <= 1e-2
+
+
+def test_normalisation_can_be_set_and_is_checked(gpu):
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        c.set_normalisation([1, 2, 3, 4], [0.5, 0.25, 2, 4], [1e-3, 2e-3, 3e-3, 4e-3])
+        assert np.array_equal(c.normalisation(),
+                              np.array([1, 2, 3, 4, 0.5, 0.25, 2, 4, 1e-3, 2e-3, 3e-3, 4e-3], dtype=np.float32))
+        for bad in (([0, 0, 0, np.nan], [1] * 4, [1] * 4), ([0] * 4, [1, 1, 0, 1], [1] * 4),
+                    ([0] * 4, [1] * 4, [1, -1, 1, 1])):
+            with pytest.raises(lbm.LbmError):
+                c.set_normalisation(*bad)
+        assert c.normalisation()[5] == np.float32(0.25)      # a refused call changes nothing
+    finally:
+        c.close()
