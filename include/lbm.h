@@ -96,6 +96,10 @@ typedef struct {
                               * rows are split evenly over the tiles); 0 = the kernel's default
                               * (block-staged: one wave of tiles filling every SM) */
     double shift_A, shift_B; /* rho0_s of the shifted storage; <= 0 means (mass_s (1 + minority)) / 2 */
+    int32_t tile_x;          /* columns per block tile of the block-staged kernel: 128 or 256;
+                              * 0 = chosen per grid (256 for 16-bit storage, and for FP32 when
+                              * the 256-column tiles are at least 64 rows tall).  Other kernels
+                              * and ensembles (128 columns) ignore it. */
 } lbm_params;
 
 /* Diagnostics of one state (Section 3).  Averages <.> run over the sub-domain
@@ -221,12 +225,18 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 /* Release the handle (and its own workspace / stream if it allocated them). */
 void lbm_destroy(lbm_handle* h);
 
-/* Pick the rows per tile (tile_y) of the handle's step kernel by timing candidate
- * values (0 = the default among them) on the handle's own grid, then use the fastest.  The state and the step
- * counter are left as they were.  cache_path: NULL, or a text file of
- * "<gpu>|<kernel>|<storage>|<nx>x<ny> <tile_y> <ms>" lines; a matching line is used
- * without timing, a new result is appended.  Outputs may be NULL. */
+/* Pick the rows per tile (tile_y) of the handle's step kernel, and for the
+ * block-staged kernel the columns per tile (tile_x, 128 or 256), by timing candidate
+ * values (0 = the default among them) on the handle's own grid, then use the
+ * fastest; lbm_get_params reports both.  The state and the step counter are left as
+ * they were.  cache_path: NULL, or a text file of
+ * "<gpu>|<kernel>|<storage>|<nx>x<ny> <tile_x> <tile_y> <ms>" lines; a matching line
+ * is used without timing, a new result is appended (lines of another form are
+ * skipped).  Outputs may be NULL. */
 lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* tile_y, double* ms_per_step);
+
+/* The handle's parameters as in use (tile_x / tile_y after lbm_tune). */
+lbm_status lbm_get_params(lbm_handle* h, lbm_params* out);
 
 /* ---- Ensembles of independent realisations (Section 2: at least 10 runs per
  * experiment).  One kernel launch per time step advances every member; chunks

@@ -811,6 +811,7 @@ lbm_status lbm_closure_coarse_params(const lbm_params* fine, lbm_params* out) {
     p.storage = LBM_STORE_F32;
     p.kernel = LBM_KERNEL_STAGED;
     p.tile_y = 0;
+    p.tile_x = 0;
     *out = p;
     return LBM_OK;
 }

@@ -63,8 +63,10 @@ struct Grid {
     size_t plane;       // elements per (component, direction) plane = ny * pitch
 };
 
-// Columns of one block tile of the block-staged kernel (one thread per column).
+// Columns of one block tile of the block-staged kernel (one thread per column): the
+// ensemble kernel's and the narrow single-grid tile, and the wide single-grid tile.
 constexpr int kBlockTileW = 128;
+constexpr int kWideTileW = 256;
 
 struct StepLaunch {
     const void* fin;
@@ -74,6 +76,7 @@ struct StepLaunch {
     Grid grid;
     Physics phys;
     int storage;         // lbm_storage
+    int tile_x;          // block-staged kernel: 128 or 256 columns per tile, 0 = chosen per grid
     int tile_y;
 };
 

@@ -29,6 +29,7 @@ class LbmParams(C.Structure):
         ("amp", C.c_double), ("width", C.c_double), ("minority", C.c_double), ("y0", C.c_double),
         ("crop_rows", C.c_int32), ("storage", C.c_int32), ("kernel", C.c_int32), ("tile_y", C.c_int32),
         ("shift_A", C.c_double), ("shift_B", C.c_double),
+        ("tile_x", C.c_int32),
     ]
 
 
@@ -75,6 +76,7 @@ _PROTOS = {
     "lbm_destroy": (None, [_h]),
     "lbm_step_noalloc": (C.c_int, [_P(LbmParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_tune": (C.c_int, [_h, C.c_char_p, _P(C.c_int32), _P(C.c_double)]),
+    "lbm_get_params": (C.c_int, [_h, _P(LbmParams)]),
     "lbm_ens_create": (C.c_int, [C.c_int32, _P(LbmParams), C.c_void_p, _P(C.c_void_p)]),
     "lbm_ens_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_ens_sync": (C.c_int, [C.c_void_p]),
@@ -313,8 +315,14 @@ class Solver:
         ty, ms = C.c_int32(), C.c_double()
         _check(self.lib.lbm_tune(self._h, str(cache_path).encode() if cache_path else None,
                                  C.byref(ty), C.byref(ms)), "lbm_tune")
-        self.params.tile_y = ty.value
+        self.params = self.get_params()
         return ty.value, ms.value
+
+    def get_params(self) -> LbmParams:
+        """The parameters as in use (tile_x / tile_y after tune())."""
+        out = LbmParams()
+        _check(self.lib.lbm_get_params(self._h, C.byref(out)), "lbm_get_params")
+        return out
 
 
 class _Member(Solver):

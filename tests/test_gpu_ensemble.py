@@ -73,14 +73,16 @@ def test_tune_keeps_state_and_caches(gpu, tmp_path):
         ref.step(7)
         f0 = s.populations()
         ty, ms = s.tune(cache)
-        assert ty > 0 and ms > 0
+        tx = s.get_params().tile_x
+        assert tx in (128, 256) and ty >= 0 and ms > 0
         assert np.array_equal(s.populations(), f0)
         assert s.step_count == 7
         s.step(20)
         ref.step(20)
         assert np.array_equal(s.populations(), ref.populations())   # the tile shape does not change the result
     text = cache.read_text().split()
-    assert int(text[1]) == ty
+    assert (int(text[1]), int(text[2])) == (tx, ty)
     with lbm.Solver(kernel="staged", **d) as s2:
         ty2, ms2 = s2.tune(cache)                                      # found in the cache, not re-timed
         assert ty2 == ty and ms2 == pytest.approx(ms, rel=1e-3)   # stored with 6 decimals
+        assert s2.get_params().tile_x == tx

@@ -53,6 +53,35 @@ def test_one_step_from_random_populations(gpu, kernel, nx, ny, tile_y):
     assert rel_err(got, ref) < 2e-6
 
 
+@pytest.mark.parametrize("tile_x", [128, 256])
+@pytest.mark.parametrize("nx,ny,tile_y", CASES)
+def test_block_tile_widths_one_step(gpu, tile_x, nx, ny, tile_y):
+    # the block-staged kernel at each of its tile widths, whatever the default picks
+    d = inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=3)
+    f = inputs.as_float32(inputs.random_populations(nx * 7 + ny, nx, ny))
+    with lbm.Solver(kernel="staged", tile_x=tile_x, tile_y=tile_y, **d) as s:
+        s.set_populations(f)
+        s.step(1)
+        got = s.populations()
+        assert s.get_params().tile_x == tile_x
+    ref = O.step(f, oracle_params(d), 1)
+    assert rel_err(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_tile_widths_give_identical_states(gpu, storage):
+    # per-site arithmetic and the stochastic rounding's random bits (site, component,
+    # time step) do not depend on the tiling: both widths and the default agree bit
+    # for bit over 25 steps, across three tiles of 256 columns with a ragged last one
+    d = inputs.params(inputs.C0, nx=600, ny=90, crop_rows=3, g=1e-4)
+    states = []
+    for tx in (0, 128, 256):
+        with lbm.Solver(kernel="staged", storage=storage, tile_x=tx, **d) as s:
+            s.step(25)
+            states.append(s.populations())
+    assert np.array_equal(states[0], states[1]) and np.array_equal(states[1], states[2])
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("extra", [
     dict(G_wall_A=0.3, G_wall_B=-0.2),                # fluid-boundary force on the wall rows
@@ -138,13 +167,14 @@ def test_tile_shape_does_not_change_the_result(gpu, kernel, tile_y):
         assert np.array_equal(a.populations(), b.populations())
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged", "warp", "pipe"])
-def test_bench_configuration_one_step_full_grid(gpu, kernel):
-    # 1024 x 2048 in the launch configurations the benchmark times (default tiles)
+@pytest.mark.parametrize("kernel,tile_x", [("fused", 0), ("staged", 0), ("staged", 256), ("warp", 0), ("pipe", 0)])
+def test_bench_configuration_one_step_full_grid(gpu, kernel, tile_x):
+    # 1024 x 2048 in the launch configurations the benchmark times (default tiles),
+    # and the block-staged kernel's wide tile
     d = inputs.params(inputs.C1, seed=2)
     p = oracle_params(d)
     f = inputs.as_float32(O.step(O.initial_populations(p), p, 1))
-    with lbm.Solver(kernel=kernel, **d) as s:
+    with lbm.Solver(kernel=kernel, tile_x=tile_x, **d) as s:
         s.set_populations(f)
         s.step(1)
         got = s.populations()
