@@ -397,34 +397,56 @@ __device__ __forceinline__ float interface_weight(const float rho[2], float2 cbu
     return 4.0f * c * (1.0f - c);
 }
 
-// Gather of the coarse run's populations after streaming (as the step kernels pull
-// them) into FP32 S [18][n], with the densities rho2 [2][n] and the total momenta
-// j2 [2][n] that the network input and the mass sums need.
-template <typename T>
-__global__ void closure_pull_kernel(const T* __restrict__ fin, Grid g, float sA, float sB, float* __restrict__ S,
-                                    float* __restrict__ rho2, float* __restrict__ j2) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= g.nx) return;
-    const float shift[2] = {sA, sB};
-    const int xm = x == 0 ? g.nx - 1 : x - 1;
-    const int xp = x == g.nx - 1 ? 0 : x + 1;
-    float f[2][9];
-    pull_site<T>(fin, g, shift, y, x, xm, xp, f);
-    const size_t n = (size_t)g.nx * g.ny, k = (size_t)y * g.nx + x;
-    float jx = 0.0f, jy = 0.0f;
+// Densities and total momentum of one site's gathered populations, summed in one
+// fixed order (the mass sums and the correction must see the same values).
+__device__ __forceinline__ void site_moments(const float f[2][9], float rho[2], float& jx, float& jy) {
+    jx = 0.0f;
+    jy = 0.0f;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         float r = 0.0f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            S[(size_t)(s * 9 + i) * n + k] = f[s][i];
             r += f[s][i];
             jx += cx(i) * f[s][i];
             jy += cy(i) * f[s][i];
         }
-        rho2[(size_t)s * n + k] = r;
+        rho[s] = r;
     }
+}
+
+// Stored slot of direction i of component s for the site (x, y) after streaming, as
+// pull_site reads it (xm / xp the periodic neighbours of x): the neighbour's slot, or
+// on a wall row the site's own slot of the opposite direction (half-way bounce-back).
+// *col receives the slot's column.
+__device__ __forceinline__ size_t pulled_slot(const Grid& g, int s, int i, int y, int x, int xm, int xp, int* col) {
+    const int sy = y - cy(i);
+    const int sx = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
+    if (cy(i) == 0 || (sy >= 0 && sy < g.ny)) {
+        *col = sx;
+        return (size_t)(s * 9 + i) * g.plane + (size_t)sy * g.pitch + g.origin + sx;
+    }
+    *col = x;
+    return (size_t)(s * 9 + opp(i)) * g.plane + (size_t)y * g.pitch + g.origin + x;
+}
+
+// Pass 1 of a correction: the densities rho2 [2][n] and total momenta j2 [2][n] of the
+// coarse run's populations after streaming (FP32 storage), gathered as the step
+// kernels pull them.
+__global__ void __launch_bounds__(128) closure_moments_kernel(const float* __restrict__ fin, Grid g,
+                                                              float* __restrict__ rho2, float* __restrict__ j2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const float zero[2] = {0.0f, 0.0f};
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9], rho[2], jx, jy;
+    pull_site<float>(fin, g, zero, y, x, xm, xp, f);
+    site_moments(f, rho, jx, jy);
+    const size_t n = (size_t)g.nx * g.ny, k = (size_t)y * g.nx + x;
+    rho2[k] = rho[0];
+    rho2[n + k] = rho[1];
     j2[k] = jx;
     j2[n + k] = jy;
 }
@@ -487,7 +509,7 @@ __global__ void __launch_bounds__(256) drho_total_kernel(double* __restrict__ pa
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        // the per-site scalars of correct_kernel, once: sum(h) / sum(w) (mode 4) and
+        // the per-site scalars of correct_inplace_kernel, once: sum(h) / sum(w) (mode 4) and
         // the mean corrections (modes 1-3), as FP32 after part[2 nparts + 1]
         const double sA = red[0][0], sB = red[1][0];
         part[2 * nparts] = sA;
@@ -503,62 +525,85 @@ __global__ void __launch_bounds__(256) drho_total_kernel(double* __restrict__ pa
 // (drho limited as above, the mean over the grid removed so that each component's
 // mass is unchanged; mode 4 removes it in proportion to the interface weight,
 // drho_A = -drho_B = h - w sum(h) / sum(w)) and u' = u_b + du in mode 1, u_b in
-// mode 2 and u_b + du / 4 in modes 3 and 4 (u_b = j / rho of S itself),
+// mode 2 and u_b + du / 4 in modes 3 and 4 (u_b = j / rho of f itself),
 //   f <- f^eq(rho'_s, u') + (rho'_s / rho_s) (f - f^eq(rho_s, u_b)),
-// i.e. the non-equilibrium part is kept in proportion to the density.  FP32 per
-// site: the corrections are small next to the populations, and the mass sums are
-// FP64.
-__global__ void __launch_bounds__(256) correct_kernel(float* __restrict__ S, const float* __restrict__ y, size_t n,
-                                                      float4 oscale, int mode, float2 cbulk,
-                                                      const float* __restrict__ scalars) {
-    // mode 4: sum(h) / sum(w); modes 1-3: the mean corrections (from drho_total_kernel)
-    const float hw = mode == 4 ? scalars[0] : 0.0f;
-    const float mA = scalars[1], mB = scalars[2];
+// i.e. the non-equilibrium part is kept in proportion to the density.  p: the
+// network output of the site in physical units (dA, dB, du_x, du_y); hw = sum(h) /
+// sum(w) (mode 4), mA / mB the mean corrections (modes 1-3).  FP32: the corrections
+// are small next to the populations, and the mass sums are FP64.
+__device__ __forceinline__ void correct_site(float f[2][9], float4 p, int mode, float2 cbulk, float hw, float mA,
+                                             float mB) {
     // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
     // full correction of mode 1 feeds back into the growing coarse modes)
     const float du = mode == 1 ? 1.0f : (mode >= 3 ? 0.25f : 0.0f);
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        float f[2][9];
-        float rho[2] = {0.0f, 0.0f}, jx = 0.0f, jy = 0.0f;
+    float rho[2], jx, jy;
+    site_moments(f, rho, jx, jy);
+    const float r = rho[0] + rho[1];
+    if (!(r > 0.0f)) return;
+    const float ux = jx / r, uy = jy / r;
+    const float vx = ux + du * p.z, vy = uy + du * p.w;
+    const float w = interface_weight(rho, cbulk);
+    float d[2];
+    limited_drho(mode, rho, p.x, p.y, w, d);
+    if (mode == 4) {
+        d[0] -= w * hw;
+        d[1] = -d[0];
+    } else {
+        d[0] -= mA;
+        d[1] -= mB;
+    }
+    const float u2 = ux * ux + uy * uy, v2 = vx * vx + vy * vy;
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 2; ++s) {
+        const float r0 = rho[s];
+        if (!(r0 > 0.0f)) continue;
+        const float r1 = fmaxf(r0 + d[s], 0.0f);
+        const float q = r1 / r0;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                f[s][i] = S[(size_t)(s * 9 + i) * n + k];
-                rho[s] += f[s][i];
-                jx += cx(i) * f[s][i];
-                jy += cy(i) * f[s][i];
-            }
-        const float r = rho[0] + rho[1];
-        if (!(r > 0.0f)) continue;
-        const float ux = jx / r, uy = jy / r;
-        const float vx = ux + du * y[2 * n + k] * oscale.z, vy = uy + du * y[3 * n + k] * oscale.w;
-        const float w = interface_weight(rho, cbulk);
-        float d[2];
-        limited_drho(mode, rho, y[k] * oscale.x, y[n + k] * oscale.y, w, d);
-        if (mode == 4) {
-            d[0] -= w * hw;
-            d[1] = -d[0];
-        } else {
-            d[0] -= mA;
-            d[1] -= mB;
-        }
-        const float u2 = ux * ux + uy * uy, v2 = vx * vx + vy * vy;
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float r0 = rho[s];
-            if (!(r0 > 0.0f)) continue;
-            const float r1 = fmaxf(r0 + d[s], 0.0f);
-            const float q = r1 / r0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float c0 = cx(i) * ux + cy(i) * uy, c1 = cx(i) * vx + cy(i) * vy;
-                const float e0 = wf(i) * r0 * (1.0f + 3.0f * c0 + 4.5f * c0 * c0 - 1.5f * u2);
-                const float e1 = wf(i) * r1 * (1.0f + 3.0f * c1 + 4.5f * c1 * c1 - 1.5f * v2);
-                S[(size_t)(s * 9 + i) * n + k] = e1 + q * (f[s][i] - e0);
-            }
+        for (int i = 0; i < 9; ++i) {
+            const float c0 = cx(i) * ux + cy(i) * uy, c1 = cx(i) * vx + cy(i) * vy;
+            const float e0 = wf(i) * r0 * (1.0f + 3.0f * c0 + 4.5f * c0 * c0 - 1.5f * u2);
+            const float e1 = wf(i) * r1 * (1.0f + 3.0f * c1 + 4.5f * c1 * c1 - 1.5f * v2);
+            f[s][i] = e1 + q * (f[s][i] - e0);
         }
     }
+}
+
+// Pass 2 of a correction, in place on the coarse run's stored FP32 populations: each
+// site gathers its 18 populations after streaming (pulled_slot), corrects them
+// (correct_site) and writes them back to the same slots, with the periodic ghost
+// copy of columns 0, 1, nx - 2, nx - 1 that the staged kernels' row windows read.
+// Every stored slot belongs to exactly one (site, direction) pair, so no two threads
+// touch the same slot; a thread's 18 loads precede its stores through one pointer.
+// scalars: sum(h) / sum(w) (mode 4) and the mean corrections (modes 1-3), from
+// drho_total_kernel.
+__global__ void __launch_bounds__(128) correct_inplace_kernel(float* pops, Grid g, const float* __restrict__ y,
+                                                              float4 oscale, int mode, float2 cbulk,
+                                                              const float* __restrict__ scalars) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = blockIdx.y;
+    if (x >= g.nx) return;
+    const int xm = x == 0 ? g.nx - 1 : x - 1;
+    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    float f[2][9];
+    int col;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[s][i] = pops[pulled_slot(g, s, i, row, x, xm, xp, &col)];
+    const size_t n = (size_t)g.nx * g.ny, k = (size_t)row * g.nx + x;
+    const float4 p = make_float4(y[k] * oscale.x, y[n + k] * oscale.y, y[2 * n + k] * oscale.z,
+                                 y[3 * n + k] * oscale.w);
+    correct_site(f, p, mode, cbulk, mode == 4 ? scalars[0] : 0.0f, scalars[1], scalars[2]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const size_t idx = pulled_slot(g, s, i, row, x, xm, xp, &col);
+            pops[idx] = f[s][i];
+            if (col < 2) pops[idx + g.nx] = f[s][i];
+            else if (col >= g.nx - 2) pops[idx - g.nx] = f[s][i];
+        }
 }
 
 }  // namespace
@@ -659,26 +704,9 @@ lbm_status set_coarse(lbm_closure* c, const float* fld) {
 
 // apply the network's correction to the coarse run (mode 1: densities and velocity,
 // mode 2: order parameter only, mode 3: order parameter and a quarter of the velocity,
-// mode 4: as mode 3 with the order parameter corrected on the interface only)
-cudaError_t launch_closure_pull(const lbm::PopView& v, float* S, float* rho2, float* j2) {
-    dim3 grid((v.grid.nx + 127) / 128, v.grid.ny);
-    switch (v.storage) {
-        case LBM_STORE_F16:
-            lbm::closure_pull_kernel<__half><<<grid, 128, 0, v.stream>>>((const __half*)v.fin, v.grid, v.shift[0],
-                                                                         v.shift[1], S, rho2, j2);
-            break;
-        case LBM_STORE_BF16:
-            lbm::closure_pull_kernel<__nv_bfloat16><<<grid, 128, 0, v.stream>>>((const __nv_bfloat16*)v.fin, v.grid,
-                                                                                v.shift[0], v.shift[1], S, rho2, j2);
-            break;
-        default:
-            lbm::closure_pull_kernel<float><<<grid, 128, 0, v.stream>>>((const float*)v.fin, v.grid, v.shift[0],
-                                                                        v.shift[1], S, rho2, j2);
-    }
-    return cudaGetLastError();
-}
-
-// clear_status: start the tensor-core kernels' status word from 0 (the first
+// mode 4: as mode 3 with the order parameter corrected on the interface only): the
+// moments, the network input and output, the mass sums, then the correction in
+// place on the stored populations.  clear_status: start the tensor-core kernels' status word from 0 (the first
 // correction of a call); later ones keep an earlier failure raised for the check
 // at the end of the call
 lbm_status correct(lbm_closure* c, int mode, bool clear_status) {
@@ -686,24 +714,25 @@ lbm_status correct(lbm_closure* c, int mode, bool clear_status) {
     const lbm_params& q = c->coarse_p;
     const double2 cbulk = make_double2(q.mass_A / (q.mass_A + q.minority * q.mass_B),
                                        q.minority * q.mass_A / (q.minority * q.mass_A + q.mass_B));
-    // the FP32 copy of the coarse populations lives in the FP64 state buffer; raw
-    // holds the densities (first half) and the momenta (second half)
-    float* Sf = reinterpret_cast<float*>(c->S);
+    const lbm::PopView v = lbm::handle_pops(c->coarse);
+    if (v.storage != LBM_STORE_F32) return cl_fail(LBM_ESTATE, "the closure's coarse run must store FP32");
+    // the coarse handle's current population buffer, which the correction rewrites in place
+    float* pops = static_cast<float*>(const_cast<void*>(v.fin));
+    // raw holds the densities (first half) and the momenta (second half)
     float* rho2 = c->raw;
     float* j2 = c->raw + 2 * c->nc;
-    CL_TRY(launch_closure_pull(lbm::handle_pops(c->coarse), Sf, rho2, j2), "pull coarse state");
+    const dim3 grid((v.grid.nx + 127) / 128, v.grid.ny);
+    lbm::closure_moments_kernel<<<grid, 128, 0, v.stream>>>(pops, v.grid, rho2, j2);
+    CL_TRY(cudaGetLastError(), "coarse moments");
     CL_TRY(lbm::handle_closure_features(c->coarse, rho2, j2, c->in_mean, c->in_scale, c->xin), "network input");
     CL_TRY(lbm::cnn_tc::infer(c->net.tc, c->params, c->xin, c->yout, c->stream, false, clear_status), "cnn inference");
     const float2 cb = make_float2((float)cbulk.x, (float)cbulk.y);
     lbm::drho_sum_kernel<<<kCorrBlocks, 256, 0, c->stream>>>(rho2, c->yout, c->nc, f4(c->out_scale), mode, cb, c->part);
     CL_TRY(cudaGetLastError(), "mass sums");
     lbm::drho_total_kernel<<<1, 256, 0, c->stream>>>(c->part, kCorrBlocks, c->nc);
-    // one site per thread: many blocks keep enough loads in flight
-    const unsigned cblocks = (unsigned)std::min<size_t>((c->nc + 255) / 256, 1u << 30);
-    lbm::correct_kernel<<<cblocks, 256, 0, c->stream>>>(Sf, c->yout, c->nc, f4(c->out_scale), mode, cb,
-                                                       reinterpret_cast<const float*>(c->part + 2 * kCorrBlocks + 2));
+    lbm::correct_inplace_kernel<<<grid, 128, 0, v.stream>>>(pops, v.grid, c->yout, f4(c->out_scale), mode, cb,
+                                                           reinterpret_cast<const float*>(c->part + 2 * kCorrBlocks + 2));
     CL_TRY(cudaGetLastError(), "correct");
-    CL_TRY(lbm::handle_push_Sf(c->coarse, Sf), "push coarse state");
     return LBM_OK;
 }
 
