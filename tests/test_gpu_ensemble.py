@@ -27,15 +27,18 @@ def member_params(m, tile_y=0):
     return lbm.default_params(kernel="staged", tile_y=tile_y, **d)
 
 
-def test_ensemble_members_equal_solo_runs(gpu):
-    params = [member_params(m, tile_y=16) for m in MEMBERS]
+# tile_y 16: 55 tiles in one partial wave; tile_y 1: 854 one-row tiles for the 608
+# resident blocks of GB300, two waves of mixed storage types
+@pytest.mark.parametrize("tile_y", [16, 1])
+def test_ensemble_members_equal_solo_runs(gpu, tile_y):
+    params = [member_params(m, tile_y=tile_y) for m in MEMBERS]
     with lbm.Ensemble(params) as ens:
         ens.step(73)                     # one 50-step graph + 23 single launches
         ens.sync()
         got = [m.populations() for m in ens.members]
         diags = ens.diagnostics()
     for m, p, g, d in zip(MEMBERS, params, got, diags):
-        with lbm.Solver(member_params(m, tile_y=16)) as s:
+        with lbm.Solver(member_params(m, tile_y=tile_y)) as s:
             s.step(73)
             want = s.populations()
         # one unit in the last place of the storage type
