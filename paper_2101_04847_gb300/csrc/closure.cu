@@ -716,8 +716,7 @@ lbm_status correct(lbm_closure* c, int mode, bool clear_status) {
                                        q.minority * q.mass_A / (q.minority * q.mass_A + q.mass_B));
     const lbm::PopView v = lbm::handle_pops(c->coarse);
     if (v.storage != LBM_STORE_F32) return cl_fail(LBM_ESTATE, "the closure's coarse run must store FP32");
-    // the coarse handle's current population buffer, which the correction rewrites in place
-    float* pops = static_cast<float*>(const_cast<void*>(v.fin));
+    float* pops = static_cast<float*>(v.pops);
     // raw holds the densities (first half) and the momenta (second half)
     float* rho2 = c->raw;
     float* j2 = c->raw + 2 * c->nc;

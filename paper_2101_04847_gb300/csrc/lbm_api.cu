@@ -332,16 +332,13 @@ cudaError_t handle_push_S(lbm_handle* h, const double* S) {
 }
 PopView handle_pops(lbm_handle* h) {
     PopView v;
-    v.fin = h->pops(h->cur);
+    v.pops = h->pops(h->cur);
     v.grid = h->grid;
     v.storage = h->p.storage;
     v.shift[0] = h->shift[0];
     v.shift[1] = h->shift[1];
     v.stream = h->stream;
     return v;
-}
-cudaError_t handle_push_Sf(lbm_handle* h, const float* S) {
-    return launch_push_from_float(S, h->grid, h->p.storage, h->shift, h->pops(h->cur), h->stream);
 }
 cudaError_t handle_closure_features(lbm_handle* h, const float* rho2, const float* j2, const float mean[4],
                                     const float scale[4], float* x) {

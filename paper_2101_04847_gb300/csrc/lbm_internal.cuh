@@ -118,10 +118,10 @@ cudaError_t handle_save_state(lbm_handle* h);
 cudaError_t handle_restore_state(lbm_handle* h);
 cudaError_t handle_fields(lbm_handle* h, const double** rA, const double** rB, const double** ux, const double** uy);
 cudaError_t handle_push_S(lbm_handle* h, const double* S);
-cudaError_t handle_push_Sf(lbm_handle* h, const float* S);   // as handle_push_S, from FP32
-// A handle's current populations as the closure's gather kernel reads them.
+// A handle's current population buffer, which the closure's correction reads and
+// rewrites in place.
 struct PopView {
-    const void* fin;
+    void* pops;
     Grid grid;
     int storage;
     float shift[2];
