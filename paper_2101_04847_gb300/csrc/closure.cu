@@ -415,21 +415,6 @@ __device__ __forceinline__ void site_moments(const float f[2][9], float rho[2], 
     }
 }
 
-// Stored slot of direction i of component s for the site (x, y) after streaming, as
-// pull_site reads it (xm / xp the periodic neighbours of x): the neighbour's slot, or
-// on a wall row the site's own slot of the opposite direction (half-way bounce-back).
-// *col receives the slot's column.
-__device__ __forceinline__ size_t pulled_slot(const Grid& g, int s, int i, int y, int x, int xm, int xp, int* col) {
-    const int sy = y - cy(i);
-    const int sx = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
-    if (cy(i) == 0 || (sy >= 0 && sy < g.ny)) {
-        *col = sx;
-        return (size_t)(s * 9 + i) * g.plane + (size_t)sy * g.pitch + g.origin + sx;
-    }
-    *col = x;
-    return (size_t)(s * 9 + opp(i)) * g.plane + (size_t)y * g.pitch + g.origin + x;
-}
-
 // Pass 1 of a correction: the densities rho2 [2][n] and total momenta j2 [2][n] of the
 // coarse run's populations after streaming (FP32 storage), gathered as the step
 // kernels pull them.
@@ -527,10 +512,14 @@ __global__ void __launch_bounds__(256) drho_total_kernel(double* __restrict__ pa
 // drho_A = -drho_B = h - w sum(h) / sum(w)) and u' = u_b + du in mode 1, u_b in
 // mode 2 and u_b + du / 4 in modes 3 and 4 (u_b = j / rho of f itself),
 //   f <- f^eq(rho'_s, u') + (rho'_s / rho_s) (f - f^eq(rho_s, u_b)),
-// i.e. the non-equilibrium part is kept in proportion to the density.  p: the
-// network output of the site in physical units (dA, dB, du_x, du_y); hw = sum(h) /
-// sum(w) (mode 4), mA / mB the mean corrections (modes 1-3).  FP32: the corrections
-// are small next to the populations, and the mass sums are FP64.
+// i.e. the non-equilibrium part is kept in proportion to the density.  With
+// q = rho'_s / rho_s, so that q rho_s = rho'_s, the two equilibria combine into
+//   f <- q f + w_i rho'_s (3 dc + 9/2 dc (c1 + c0) - 3/2 (u'.u' - u_b.u_b)),
+// c0 = c_i.u_b, c1 = c_i.u', dc = c1 - c0 (a few operations per population instead
+// of two equilibria).  p: the network output of the site in physical units (dA, dB,
+// du_x, du_y); hw = sum(h) / sum(w) (mode 4), mA / mB the mean corrections (modes
+// 1-3).  FP32: the corrections are small next to the populations, and the mass sums
+// are FP64.
 __device__ __forceinline__ void correct_site(float f[2][9], float4 p, int mode, float2 cbulk, float hw, float mA,
                                              float mB) {
     // mode 2 keeps the velocity; modes 3 and 4 relax it a quarter of the way (the
@@ -552,7 +541,7 @@ __device__ __forceinline__ void correct_site(float f[2][9], float4 p, int mode, 
         d[0] -= mA;
         d[1] -= mB;
     }
-    const float u2 = ux * ux + uy * uy, v2 = vx * vx + vy * vy;
+    const float du2 = 1.5f * ((vx * vx + vy * vy) - (ux * ux + uy * uy));
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const float r0 = rho[s];
@@ -562,47 +551,67 @@ __device__ __forceinline__ void correct_site(float f[2][9], float4 p, int mode, 
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float c0 = cx(i) * ux + cy(i) * uy, c1 = cx(i) * vx + cy(i) * vy;
-            const float e0 = wf(i) * r0 * (1.0f + 3.0f * c0 + 4.5f * c0 * c0 - 1.5f * u2);
-            const float e1 = wf(i) * r1 * (1.0f + 3.0f * c1 + 4.5f * c1 * c1 - 1.5f * v2);
-            f[s][i] = e1 + q * (f[s][i] - e0);
+            const float dc = c1 - c0;
+            f[s][i] = q * f[s][i] + wf(i) * r1 * (3.0f * dc + 4.5f * dc * (c1 + c0) - du2);
         }
     }
 }
 
 // Pass 2 of a correction, in place on the coarse run's stored FP32 populations: each
-// site gathers its 18 populations after streaming (pulled_slot), corrects them
-// (correct_site) and writes them back to the same slots, with the periodic ghost
-// copy of columns 0, 1, nx - 2, nx - 1 that the staged kernels' row windows read.
-// Every stored slot belongs to exactly one (site, direction) pair, so no two threads
-// touch the same slot; a thread's 18 loads precede its stores through one pointer.
-// scalars: sum(h) / sum(w) (mode 4) and the mean corrections (modes 1-3), from
-// drho_total_kernel.
-__global__ void __launch_bounds__(128) correct_inplace_kernel(float* pops, Grid g, const float* __restrict__ y,
+// site gathers its 18 populations after streaming from the slots pull_site reads
+// (addressed from one site pointer: slot = site + plane offset - c_iy pitch + the
+// periodic column offset, or the site's own slot of the opposite direction on a
+// wall row), corrects them (correct_site) and writes them back to the same slots,
+// with the periodic ghost copy of columns 0, 1, nx - 2, nx - 1 that the staged
+// kernels' row windows read.  Every stored slot belongs to exactly one (site,
+// direction) pair, so no two threads touch the same slot; a thread's 18 loads
+// precede its stores through one pointer.  scalars: sum(h) / sum(w) (mode 4) and the
+// mean corrections (modes 1-3), from drho_total_kernel.
+__global__ void __launch_bounds__(128, 7) correct_inplace_kernel(float* pops, Grid g, const float* __restrict__ y,
                                                               float4 oscale, int mode, float2 cbulk,
                                                               const float* __restrict__ scalars) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = blockIdx.y;
     if (x >= g.nx) return;
-    const int xm = x == 0 ? g.nx - 1 : x - 1;
-    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    // column offsets of the west and east neighbours (periodic)
+    const int dxw = x == 0 ? g.nx - 1 : -1;
+    const int dxe = x == g.nx - 1 ? 1 - g.nx : 1;
+    const bool bottom = row == 0, top = row == g.ny - 1;
+    const ptrdiff_t plane = (ptrdiff_t)g.plane, pitch = g.pitch;
+    float* const site = pops + (ptrdiff_t)row * pitch + g.origin + x;
+    // slot of direction i of component s, and the slot's column offset from x
+    auto slot = [&](int s, int i, int* dcol) -> float* {
+        if ((cy(i) == 1 && bottom) || (cy(i) == -1 && top)) {
+            *dcol = 0;
+            return site + (s * 9 + opp(i)) * plane;
+        }
+        *dcol = cx(i) == 0 ? 0 : (cx(i) == 1 ? dxw : dxe);
+        return site + (s * 9 + i) * plane - cy(i) * pitch + *dcol;
+    };
     float f[2][9];
-    int col;
+    int dcol;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[s][i] = pops[pulled_slot(g, s, i, row, x, xm, xp, &col)];
+        for (int i = 0; i < 9; ++i) f[s][i] = *slot(s, i, &dcol);
     const size_t n = (size_t)g.nx * g.ny, k = (size_t)row * g.nx + x;
     const float4 p = make_float4(y[k] * oscale.x, y[n + k] * oscale.y, y[2 * n + k] * oscale.z,
                                  y[3 * n + k] * oscale.w);
     correct_site(f, p, mode, cbulk, mode == 4 ? scalars[0] : 0.0f, scalars[1], scalars[2]);
+    // ghost copies: only the threads of the first / last three columns can write a
+    // slot in columns 0, 1, nx - 2, nx - 1
+    const bool edge = x < 3 || x >= g.nx - 3;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const size_t idx = pulled_slot(g, s, i, row, x, xm, xp, &col);
-            pops[idx] = f[s][i];
-            if (col < 2) pops[idx + g.nx] = f[s][i];
-            else if (col >= g.nx - 2) pops[idx - g.nx] = f[s][i];
+            float* q = slot(s, i, &dcol);
+            *q = f[s][i];
+            if (edge) {
+                const int col = x + dcol;
+                if (col < 2) q[g.nx] = f[s][i];
+                else if (col >= g.nx - 2) q[-g.nx] = f[s][i];
+            }
         }
 }
 

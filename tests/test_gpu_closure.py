@@ -230,7 +230,7 @@ def test_one_correction_matches_the_oracle(gpu, mode):
     # where a stored input or activation rounds to the other BF16 neighbour in the two
     # evaluations (its FP32 and FP64 values straddle a rounding boundary), a 3 x 3 to
     # 5 x 5 patch of outputs moves, each by well under 1 % of the largest increment
-    # (measured, modes 1-4: median 0.8-2.9e-7, 0.4-0.9 % of the values beyond 1e-4,
+    # (measured, modes 1-4: median 0.5-1.7e-7, 0.4-0.9 % of the values beyond 1e-4,
     # the largest 1.7-4.4e-3 of the largest increment)
     assert off <= 0.05
     assert err.max() <= 1e-2 * big
