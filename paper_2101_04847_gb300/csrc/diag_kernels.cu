@@ -466,11 +466,14 @@ __device__ __forceinline__ void nbr_sum_f(const float* __restrict__ r, const Fea
     sy = (N - S) * (1.0f / 9.0f) + (d + (NW - SE)) * (1.0f / 36.0f);
 }
 
-// the same force and physical velocity as the diagnostics' velocity pass, in FP32
-__global__ void __launch_bounds__(256) closure_features_kernel(FeatArgs a, const float* __restrict__ rho2,
+// the same force and physical velocity as the diagnostics' velocity pass, in FP32;
+// one thread per column, rows y = blockIdx.y, blockIdx.y + gridDim.y, ...
+__global__ void __launch_bounds__(128) closure_features_kernel(FeatArgs a, const float* __restrict__ rho2,
                                                                 const float* __restrict__ j2, float* __restrict__ xo) {
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n; k += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(k / a.nx), x = (int)(k % a.nx);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.nx) return;
+    for (int y = blockIdx.y; y < a.ny; y += gridDim.y) {
+        const size_t k = (size_t)y * a.nx + x;
         const float jx = j2[k], jy = j2[a.n + k];
         const float rA = rho2[k], rB = rho2[a.n + k];
         float nAx, nAy, nBx, nBy;
@@ -508,8 +511,8 @@ cudaError_t launch_closure_features(const DiagLaunch& D, const float* rho2, cons
         a.mean[c] = mean[c];
         a.scale[c] = scale[c];
     }
-    const int blocks = (int)std::min<size_t>(4096, (a.n + 255) / 256);
-    closure_features_kernel<<<blocks, 256, 0, st>>>(a, rho2, j2, x);
+    const dim3 grid((a.nx + 127) / 128, std::min(a.ny, 65535));
+    closure_features_kernel<<<grid, 128, 0, st>>>(a, rho2, j2, x);
     return cudaGetLastError();
 }
 
