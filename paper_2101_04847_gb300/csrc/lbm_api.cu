@@ -422,7 +422,8 @@ extern "C" lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* t
             if (ty > h->p.ny && ty != cand[0]) break;
             h->p.tile_x = xs[ix];
             h->p.tile_y = ty;
-            const int reps = 10;
+            // 30 steps per candidate: the two tile widths can differ by well under 1 %
+            const int reps = 30;
             lbm_status st = launch_steps(h, 2);
             if (st == LBM_OK) {
                 cudaEventRecord(a, h->stream);
