@@ -274,6 +274,32 @@ def test_advance_is_the_steps_then_the_correction(gpu):
     assert rms <= 1e-2
 
 
+def test_in_place_correction_keeps_the_ghost_columns(gpu):
+    # the correction rewrites the stored populations in place, periodic ghost
+    # columns included; the staged step kernel reads those ghosts at the tile edges
+    # (the 64-column coarse grid is one tile, so every step reads columns -2, -1, nx
+    # and nx + 1).  Steps after the correction must equal steps from the same
+    # populations loaded through set_populations, which writes the ghosts itself.
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        pc, f0, p32, (in_mean, in_scale, out_scale) = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(in_mean, in_scale, out_scale)
+        _, co = c.solvers()
+        co.set_populations(f0.astype(np.float32))
+        c.correct(4)
+        corrected = co.populations(np.empty(f0.shape, dtype=np.float32))
+        assert not np.array_equal(corrected, f0.astype(np.float32))
+        co.step(5)
+        after = co.populations()
+        co.set_populations(corrected)
+        co.step(5)
+        again = co.populations()
+    finally:
+        c.close()
+    assert np.array_equal(after, again)
+
+
 def test_normalisation_can_be_set_and_is_checked(gpu):
     c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
     try:
