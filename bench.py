@@ -606,7 +606,7 @@ def run_closure_accuracy(args):
                               g=3e-4, n_modes=8, amp=4.0, width=1.5, minority=0.08, crop_rows=10, seed=1)
     c = lbm.Closure(fine, interval=10, seed=0)
     t0 = time.time()
-    c.generate(n_runs=6, seed0=11, warmup=200, intervals=8)
+    c.generate(n_runs=args.closure_runs, seed0=11, warmup=200, intervals=8)
     loss = [c.train(epochs=1, lr=2e-3, shuffle_seed=e) for e in range(25)]
     train_s = time.time() - t0
 
@@ -629,7 +629,7 @@ def run_closure_accuracy(args):
                 res[seed][mode] = f"status {ex.status}"
     c.close()
     print(json.dumps({"kind": "closure_accuracy", "fine": f"{args.nx}x{args.ny}", "coarse": f"{args.nx // 2}x{args.ny // 2}",
-                      "intervals": args.closure_intervals,
+                      "intervals": args.closure_intervals, "training_runs": args.closure_runs,
                       "train": {"loss_first": round(loss[0], 4), "loss_last": round(loss[-1], 4), "seconds": round(train_s, 1)},
                       "relative_rms_error_vs_fine": res}), flush=True)
 
@@ -654,6 +654,8 @@ def main():
                     help="train the closure on the --nx x --ny fine grid and compare held-out coarse runs with the fine run")
     ap.add_argument("--closure-intervals", dest="closure_intervals", type=int, default=12,
                     help="with --closure-accuracy: intervals of 10 coarse steps in each held-out run")
+    ap.add_argument("--closure-runs", dest="closure_runs", type=int, default=6,
+                    help="seeded fine runs that provide the closure's training pairs (8 intervals each)")
     ap.add_argument("--closure", action="store_true",
                     help="time the learned closure (coarse run + correction) against the plain fine solver")
     ap.add_argument("--storage-study", dest="storage_study", type=int, default=0,
