@@ -365,7 +365,8 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
  *   u' = u_b + a du, a = 1 (mode 1), 0 (mode 2), 1/4 (modes 3, 4);
  *   rho'_s = max(rho_s + d_s, 0),
  *   f_i^s <- f_i^eq(rho'_s, u') + (rho'_s / rho_s) (f_i^s - f_i^eq(rho_s, u_b)).
- * Arithmetic in FP32 per site, the grid sums in FP64. */
+ * Arithmetic in FP32 per site; the grid sums are compensated FP32 sums per thread,
+ * added in FP64 across threads. */
 lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_net);
 
 /* One correction (mode use_net, as above) of the coarse run's current state, with
