@@ -26,7 +26,10 @@ One time step (Section 2, "Kinetic equation" and "Equilibrium distribution"):
 Readings of points the paper leaves open:
   * bounce-back variant: half-way (the paper only says "bounce-back");
   * the pseudopotential of a wall node is 0 (no fluid in the solid), and the
-    wall indicator S is 1 on the virtual rows y = -1 and y = ny;
+    wall indicator S is 1 on the virtual rows y = -1 and y = ny; wall_mode = 1
+    instead mirrors the pseudopotential across the wall (the virtual row y = -1
+    holds row 0's values, y = ny row ny - 1's), a neutral wall that exerts no
+    Shan-Chen force on a uniform fluid;
   * weights are the textbook solution 4/9, 1/9, 1/36 of the isotropy
     conditions printed after the equilibrium distribution (pinned by a test);
   * diagnostic velocity: u_phys = (sum_{s,i} f c + F/2) / rho;
@@ -80,6 +83,7 @@ class Params:
     minority: float = 0.08    # epsilon: fraction of the other component in each bulk
     y0: float | None = None   # mean interface height (default ny / 2)
     crop_rows: int = 10       # rows cut at top and bottom for averages (Section 3)
+    wall_mode: int = 0        # pseudopotential beyond a wall: 0 = none (psi = 0), 1 = mirror of the wall row
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -186,12 +190,17 @@ def common_velocity(f: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
     return num_x / den, num_y / den
 
 
-def neighbour_sum(field: np.ndarray, ghost: float) -> tuple[np.ndarray, np.ndarray]:
+def neighbour_sum(field: np.ndarray, ghost: float | None) -> tuple[np.ndarray, np.ndarray]:
     """sum_i w_i field(x + c_i) c_i (both components of the vector), with x periodic
-    and `ghost` as the value on the virtual wall rows y = -1 and y = ny."""
+    and `ghost` as the value on the virtual wall rows y = -1 and y = ny (None: the
+    wall rows' own values, mirrored across the walls)."""
     ny, nx = field.shape
-    padded = np.full((ny + 2, nx), ghost, dtype=np.float64)
+    padded = np.empty((ny + 2, nx), dtype=np.float64)
     padded[1:-1] = field
+    if ghost is None:
+        padded[0], padded[-1] = field[0], field[-1]
+    else:
+        padded[0], padded[-1] = ghost, ghost
     sx = np.zeros((ny, nx))
     sy = np.zeros((ny, nx))
     for i in range(1, 9):
@@ -206,7 +215,8 @@ def forces(f: np.ndarray, p: Params) -> np.ndarray:
     """F_s = F_s^ff + F_s^fb + F_s^ext, shape (2 components, 2 axes, ny, nx).
 
     F_s^ff = -G rho_s sum_i w_i rho_s'(x + c_i) c_i  (Eq. "Shan-Chen forcing term", psi = rho,
-             no self-interaction; the pseudopotential of a wall node is 0)
+             no self-interaction; the pseudopotential of a wall node is 0, or with
+             wall_mode = 1 that of the fluid node it mirrors)
     F_s^fb = -G_sb rho_s sum_i w_i S(x + c_i) c_i   (fluid-boundary force, S = 1 on wall nodes)
     F_A^ext = -rho_A g e_y, F_B^ext = +rho_B g e_y  (Eq. 3_Fex; gravity_mode = 1 gives both -rho_s g e_y)
     plus rho_s gx e_x (a test-only body force).
@@ -221,7 +231,7 @@ def forces(f: np.ndarray, p: Params) -> np.ndarray:
         gsign = (-1.0, -1.0)
     F = np.zeros((2, 2, ny, nx))
     for s in range(2):
-        other_x, other_y = neighbour_sum(rho[1 - s], ghost=0.0)
+        other_x, other_y = neighbour_sum(rho[1 - s], ghost=None if p.wall_mode == 1 else 0.0)
         F[s, 0] = -p.G * rho[s] * other_x - gwall[s] * rho[s] * wall_x + rho[s] * p.gx
         F[s, 1] = -p.G * rho[s] * other_y - gwall[s] * rho[s] * wall_y + gsign[s] * rho[s] * p.g
     return F
@@ -358,6 +368,36 @@ def diagnostics(f: np.ndarray, p: Params) -> dict:
     return out
 
 
+def spurious_coefficient(tau: float) -> float:
+    """cs^4 (tau - 1/2)^2, the prefactor of the spurious stress K^(tau) (Section 3, Eq. "Three
+    parts of the pressure tensor")."""
+    return CS2 * CS2 * (tau - 0.5) ** 2
+
+
+def stress_tensors(rhoA: np.ndarray, rhoB: np.ndarray, p: Params) -> dict:
+    """The three parts of the pressure tensor of Section 3 (Eq. "Three parts of the pressure
+    tensor") on the grid, derivatives by centred differences (NaN on the wall rows):
+      p_b  = cs^2 rho + G cs^2 (rho^2 - phi^2) / 4                       (bulk pressure)
+      P^K  = [-k phi lap phi - k/2 |grad phi|^2] I + k grad phi (x) grad phi, k = cs^4 G / 4
+      K^tau = cs^4 (tau - 1/2)^2 rho_A rho_B / rho  v (x) v,  v = grad rho_A / rho_A - grad rho_B / rho_B
+    K^tau is evaluated as (rho_B grad rho_A - rho_A grad rho_B) (x) (...) / (rho_A rho_B rho) with
+    rho_A rho_B clamped at 1e-12; tau is the mean of the two relaxation times."""
+    rho = rhoA + rhoB
+    phi = rhoA - rhoB
+    tau = 0.5 * (p.tau_A + p.tau_B)
+    kappa = CS2 * CS2 * p.G / 4.0
+    pb = CS2 * rho + p.G * CS2 / 4.0 * (rho * rho - phi * phi)
+    phx, phy = ddx(phi), ddy(phi)
+    iso = -kappa * phi * laplacian(phi) - 0.5 * kappa * (phx * phx + phy * phy)
+    prod = np.maximum(rhoA * rhoB, 1e-12)
+    vx = rhoB * ddx(rhoA) - rhoA * ddx(rhoB)
+    vy = rhoB * ddy(rhoA) - rhoA * ddy(rhoB)
+    coef = spurious_coefficient(tau) / (prod * rho)
+    return dict(pb=pb,
+                PKxx=iso + kappa * phx * phx, PKxy=kappa * phx * phy, PKyy=iso + kappa * phy * phy,
+                Kxx=coef * vx * vx, Kxy=coef * vx * vy, Kyy=coef * vy * vy)
+
+
 def field_diagnostics(rhoA: np.ndarray, rhoB: np.ndarray, ux: np.ndarray, uy: np.ndarray, p: Params) -> dict:
     """Diagnostic terms of Section 3 from the density and velocity fields.
 
@@ -370,7 +410,8 @@ def field_diagnostics(rhoA: np.ndarray, rhoB: np.ndarray, ux: np.ndarray, uy: np
       flux_tau = <u . div K^tau>, K^tau = cs^4 rho_A rho_B / rho (tau-1/2)^2 v (x) v, v = grad rho_A / rho_A - grad rho_B / rho_B
       viscous = <u . div(eta grad u + eta grad u^T)>, eta = rho_bar cs^2 (tau - 1/2)
       enstrophy = 1/2 sum omega^2, omega = d_x u_y - d_y u_x  (Section 3, "Viscous dissipation and enstrophy")
-      h: mixing-layer width of the row means of phi; L_int: Cauchy-Crofton length of {phi = 0}.
+      h: mixing-layer width (6 sum c(1-c)) of the normalised row means of the mass fraction
+         c = rho_A / (rho_A + rho_B); L_int: Cauchy-Crofton length of {phi = 0}.
     """
     rho = rhoA + rhoB
     phi = rhoA - rhoB
@@ -383,27 +424,12 @@ def field_diagnostics(rhoA: np.ndarray, rhoB: np.ndarray, ux: np.ndarray, uy: np
 
     y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
     tau = 0.5 * (p.tau_A + p.tau_B)
-    kappa = CS2 * CS2 * p.G / 4.0
 
-    # bulk pressure
-    pb = CS2 * rho + p.G * CS2 / 4.0 * (rho * rho - phi * phi)
+    T = stress_tensors(rhoA, rhoB, p)
+    pb = T["pb"]
     flux_pb = mean(ux * ddx(pb) + uy * ddy(pb))
-
-    # Korteweg stress
-    phx, phy = ddx(phi), ddy(phi)
-    iso = -kappa * phi * laplacian(phi) - 0.5 * kappa * (phx * phx + phy * phy)
-    Pxx = iso + kappa * phx * phx
-    Pxy = kappa * phx * phy
-    Pyy = iso + kappa * phy * phy
-    flux_K = mean(ux * (ddx(Pxx) + ddy(Pxy)) + uy * (ddx(Pxy) + ddy(Pyy)))
-
-    # spurious tau-dependent stress
-    prod = np.maximum(rhoA * rhoB, 1e-12)
-    vx = rhoB * ddx(rhoA) - rhoA * ddx(rhoB)
-    vy = rhoB * ddy(rhoA) - rhoA * ddy(rhoB)
-    coef = CS2 * CS2 * (tau - 0.5) ** 2 / (prod * rho)
-    Kxx, Kxy, Kyy = coef * vx * vx, coef * vx * vy, coef * vy * vy
-    flux_tau = mean(ux * (ddx(Kxx) + ddy(Kxy)) + uy * (ddx(Kxy) + ddy(Kyy)))
+    flux_K = mean(ux * (ddx(T["PKxx"]) + ddy(T["PKxy"])) + uy * (ddx(T["PKxy"]) + ddy(T["PKyy"])))
+    flux_tau = mean(ux * (ddx(T["Kxx"]) + ddy(T["Kxy"])) + uy * (ddx(T["Kxy"]) + ddy(T["Kyy"])))
 
     # viscous term
     rho_bar = mean(rho)
