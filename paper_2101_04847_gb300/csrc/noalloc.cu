@@ -9,6 +9,7 @@
 #include "collide.cuh"
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -16,11 +17,13 @@ namespace lbm {
 namespace {
 
 constexpr int kNoAllocMaxSites = 1 << 20;     // largest nx * ny accepted
+constexpr int kNoAllocMaxRows = 65535;          // gridDim.y limit: the kernels run one block row per grid row
 constexpr int kNoAllocMaxDevices = 64;
 
 // Density scratch: rho_A at [0, n), rho_B at [n, 2n); the int after the densities is
-// the status word of the guard.  Every GPU that loads the library holds these
-// 8 MiB until the process exits.
+// where the collision's guard writes its status (nothing reads it: this entry point
+// makes no NaN / negative-density report).  Every GPU that loads the library holds
+// these 8 MiB until the process exits.
 static __device__ __align__(256) float g_noalloc_scratch[2 * kNoAllocMaxSites + 64];
 
 std::mutex g_noalloc_mu;
@@ -109,14 +112,25 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in
     if (!p || !pops_in || !pops_out) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: NULL argument");
     if (pops_in == pops_out) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: pops_in and pops_out must differ");
     if (p->nx < 4 || p->ny < 8) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: nx must be >= 4 and ny >= 8");
+    if (p->ny > kNoAllocMaxRows)
+        return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: ny = " + std::to_string(p->ny) + " exceeds " +
+                                            std::to_string(kNoAllocMaxRows) + " rows (one grid row per launch row)");
     if ((int64_t)p->nx * p->ny > kNoAllocMaxSites)
         return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: nx * ny = " + std::to_string((int64_t)p->nx * p->ny) +
                                             " exceeds the fixed scratch of " + std::to_string(kNoAllocMaxSites) +
                                             " sites; use lbm_step on a handle");
     if (p->storage != LBM_STORE_F32) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: FP32 populations only");
+    {
+        const uintptr_t bytes = (uintptr_t)18 * (uintptr_t)p->nx * (uintptr_t)p->ny * sizeof(float);
+        const uintptr_t a = (uintptr_t)pops_in, b = (uintptr_t)pops_out;
+        if (a < b + bytes && b < a + bytes)
+            return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: pops_in and pops_out overlap");
+    }
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: tau must be > 0.5");
     if (p->gravity_mode < 0 || p->gravity_mode > 1)
         return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: gravity_mode must be 0 or 1");
+    if (p->wall_mode < 0 || p->wall_mode > 1)
+        return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: wall_mode must be 0 or 1");
     const double vals[] = {p->G, p->G_wall_A, p->G_wall_B, p->g, p->gx};
     for (double v : vals)
         if (!std::isfinite(v)) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: parameters must be finite");
@@ -125,17 +139,30 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(LBM_EINVAL, "lbm_step_noalloc: device index too large");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // an error left by the caller's earlier work is reported, not cleared or taken as ours
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return noalloc_fail(LBM_ECUDA, std::string("lbm_step_noalloc: a CUDA error was pending before the call: ") +
+                                           cudaGetErrorString(e));
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &capture);
+    if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     float* scratch = nullptr;
     {
-        // first call on this device: resolve the device address of the scratch array
-        // (the host-side name is only a stand-in for it)
+        // The host-side name of the scratch array is only a stand-in: its device address
+        // belongs to the context that is current.  Outside a stream capture every call looks
+        // it up again, so a device reset or another context on the same device gets the
+        // address that is valid there; inside a capture the address of the last call made
+        // outside one on this device is used.
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            e = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_noalloc_ptr[dev] = nullptr;
-                return noalloc_fail(LBM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            }
+        if (capture == cudaStreamCaptureStatusNone) {
+            float* addr = nullptr;
+            e = cudaGetSymbolAddress((void**)&addr, g_noalloc_scratch);
+            if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = addr;
+        } else if (!g_noalloc_ptr[dev]) {
+            return noalloc_fail(LBM_ESTATE, "lbm_step_noalloc: the first call on a device must come before any stream capture");
         }
         scratch = g_noalloc_ptr[dev];
     }
@@ -156,18 +183,18 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in
     ph.ay_ext[0] = (float)(-p->g);
     ph.ay_ext[1] = (float)(p->gravity_mode == 0 ? p->g : -p->g);
     ph.ax_ext = (float)p->gx;
+    ph.wall_mirror = p->wall_mode == 1 ? 1 : 0;
     ph.shift[0] = ph.shift[1] = 0.0f;
     ph.rho_floor[0] = ph.rho_floor[1] = 0.0f;
     ph.step_in = nullptr;
     ph.step_out = nullptr;
 
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    e = cudaMemsetAsync(flag, 0, sizeof(int), st);   // the status word starts at zero on every call
-    if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("clear status: ") + cudaGetErrorString(e));
     dim3 grid((nx + kThreadsX - 1) / kThreadsX, ny);
     noalloc_density_kernel<<<grid, kThreadsX, 0, st>>>(pops_in, nx, ny, rho);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("lbm_step_noalloc: density kernel launch: ") + cudaGetErrorString(e));
     noalloc_collide_push_kernel<<<grid, kThreadsX, 0, st>>>(pops_in, pops_out, rho, ph, nx, ny, flag);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("lbm_step_noalloc launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, std::string("lbm_step_noalloc: collide/push kernel launch: ") + cudaGetErrorString(e));
     return LBM_OK;
 }

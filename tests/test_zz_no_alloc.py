@@ -63,3 +63,13 @@ def test_noalloc_rejects_grids_beyond_its_scratch(gpu):
     p = lbm.default_params(nx=64, ny=64, storage="f16")
     assert lib.lbm_step_noalloc(C.byref(p), C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), None) == lbm.LBM_EINVAL
     assert lib.lbm_step_noalloc(C.byref(p), C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), None) == lbm.LBM_EINVAL
+    # more rows than a launch grid has (within the scratch size)
+    p = lbm.default_params(nx=4, ny=70000)
+    assert lib.lbm_step_noalloc(C.byref(p), C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), None) == lbm.LBM_EINVAL
+    assert b"rows" in lib.lbm_last_error()
+    # output overlapping the input by part of its length
+    big = torch.empty(2 * 18 * 64 * 64, dtype=torch.float32, device="cuda")
+    p = lbm.default_params(nx=64, ny=64)
+    st = lib.lbm_step_noalloc(C.byref(p), C.c_void_p(big.data_ptr()), C.c_void_p(big.data_ptr() + 4 * 1000), None)
+    assert st == lbm.LBM_EINVAL
+    assert b"overlap" in lib.lbm_last_error()
