@@ -100,6 +100,10 @@ typedef struct {
                               * 0 = chosen per grid (256 for 16-bit storage, and for FP32 when
                               * the 256-column tiles are at least 64 rows tall).  Other kernels
                               * and ensembles (128 columns) ignore it. */
+    int32_t wall_mode;       /* pseudopotential beyond the walls in the Shan-Chen force (Section 2
+                              * leaves it open): 0 = none (psi = 0 on the virtual rows y = -1 and
+                              * y = ny); 1 = mirror (those rows hold the wall rows' own psi: a
+                              * neutral wall that exerts no force on a uniform fluid) */
 } lbm_params;
 
 /* Diagnostics of one state (Section 3).  Averages <.> run over the sub-domain
@@ -171,6 +175,15 @@ lbm_status lbm_sync(lbm_handle* h);
 
 /* Current time step of the state. */
 lbm_status lbm_step_count(lbm_handle* h, int64_t* step);
+
+/* Test of the step kernels' timeout path (no counterpart in the paper): one launch of
+ * the block-staged FP32 step with its bulk row copies withheld and its waits limited
+ * to a few thousand polls, so that every wait gives up and raises the guard's timeout
+ * bit with nothing in flight.  It writes garbage to the buffer the next step writes
+ * and leaves the current state and the step count unchanged; the next lbm_sync or
+ * lbm_diagnostics returns LBM_ETIMEOUT, which stays raised until lbm_reset.
+ * FP32 storage only (else LBM_EINVAL); asynchronous. */
+lbm_status lbm_step_test_timeout(lbm_handle* h);
 
 /* Diagnostics of the current state (Section 3); synchronises.  *out is filled
  * even when the returned status is LBM_EUNSTABLE. */
@@ -376,6 +389,30 @@ lbm_status lbm_closure_advance(lbm_closure* c, int32_t intervals, int32_t use_ne
  * LBM_ETIMEOUT as lbm_closure_advance does. */
 lbm_status lbm_closure_correct(lbm_closure* c, int32_t use_net);
 
+/* The closure in production, the call the method's workload makes (an extension:
+ * the paper has no learned closure): advance the coarse run by coarse_steps coarse
+ * steps (each worth four fine steps), correcting it with mode 4 (lbm_closure_advance)
+ * after every full interval, then write the coarse run's diagnostics to *out.
+ * Needs trained or set parameters (else LBM_ESTATE).  Synchronises the closure's
+ * stream.
+ *
+ * The fine plain solver is the fallback.  The call first saves the coarse fields
+ * (rho_A, rho_B, u).  If at the end the coarse run's guard reports a NaN or a
+ * negative density, or a bounded wait of the tensor-core kernels gave up, the fine
+ * solver restarts from those fields, prolonged bilinearly to the fine grid (mass of
+ * each component kept, velocities halved to fine lattice units) at equilibrium, runs
+ * 4 * coarse_steps fine steps, and the coarse run restarts from the restriction of
+ * the result (2 x 2 block means, the velocity momentum-weighted); the call then
+ * returns LBM_OK with the diagnostics of that state and lbm_closure_fallbacks counts
+ * one more.  The first fallback allocates the fine buffers it needs: 16 floats of
+ * fields and 72 doubles of populations per coarse site.
+ * An instability of the fine run itself is returned (LBM_EUNSTABLE).  Shorter calls
+ * lose less work to a fallback. */
+lbm_status lbm_closure_run(lbm_closure* c, int64_t coarse_steps, lbm_diag* out);
+
+/* How many lbm_closure_run calls fell back to the fine solver. */
+lbm_status lbm_closure_fallbacks(lbm_closure* c, int64_t* count);
+
 /* Copy the network parameters to (set = 0) or from (set = 1) host memory. */
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set);
 
@@ -399,21 +436,28 @@ void lbm_closure_destroy(lbm_closure* c);
  * has no counterpart; this is an embedding interface.
  *
  * Same physics and FP32 arithmetic as lbm_step (the two-pass form: a density pass,
- * then collision and streaming).  pops_in and pops_out are distinct device arrays
- * of 2*9*ny*nx floats, [component][direction][y][x], holding post-streaming
- * populations (the layout of lbm_get_populations, in FP32); pops_out receives the
- * populations one step later.  Only nx, ny, tau_A, tau_B, G, G_wall_A, G_wall_B,
- * g, gravity_mode and gx of *p are used; storage must be LBM_STORE_F32.
+ * then collision and streaming).  pops_in and pops_out are device arrays of
+ * 2*9*ny*nx floats, [component][direction][y][x], holding post-streaming
+ * populations (the layout of lbm_get_populations, in FP32); they must not overlap
+ * at all (LBM_EINVAL if they do).  pops_out receives the populations one step
+ * later.  Only nx, ny, tau_A, tau_B, G, G_wall_A, G_wall_B, g, gravity_mode, gx
+ * and wall_mode of *p are used; storage must be LBM_STORE_F32; 4 <= nx, 8 <= ny <= 65535.
  * cuda_stream: a cudaStream_t, or NULL for the default stream.  Asynchronous.
+ * A CUDA error already pending when the call is made is returned as LBM_ECUDA
+ * (and left pending); a launch failure is returned as LBM_ECUDA naming the kernel.
  *
  * Scratch: the densities go to a fixed device array inside the library of
  * 2 * 2^20 floats (8 MiB), held by every GPU that loads the library until the
- * process exits; grids with nx * ny > 2^20 are rejected with LBM_EINVAL.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress),
- * so make the first call on each device before any stream capture.  All calls
- * share the array: calls whose kernels overlap on the GPU (different streams, or
- * threads) race and give wrong results; serialise them.  No NaN / negative-density
- * report: use lbm_step on a handle for that. */
+ * process exits; grids with nx * ny > 2^20 are rejected with LBM_EINVAL.  A call
+ * made outside a stream capture looks up that array's device address in the
+ * current context (cudaGetSymbolAddress) and remembers it for the device; a call
+ * made while cuda_stream is capturing uses the remembered address, so make one
+ * call on each device before any stream capture, and again after a device reset
+ * (cudaDeviceReset) or a switch to another context on that device, which
+ * invalidate it (LBM_ESTATE if no address is remembered).  All calls share the
+ * array: calls whose kernels overlap on the GPU (different streams, or threads)
+ * race and give wrong results; serialise them.  No NaN / negative-density report:
+ * use lbm_step on a handle for that. */
 lbm_status lbm_step_noalloc(const lbm_params* p, const float* pops_in, float* pops_out, void* cuda_stream);
 
 #ifdef __cplusplus

@@ -357,6 +357,29 @@ __global__ void fields_to_populations_kernel(const float* __restrict__ fld, size
     }
 }
 
+// Fine fields from coarse fields (the fallback's restart): bilinear in the cell
+// centres (coarse cell X covers fine columns 2X and 2X + 1, so fine column x sits at
+// coarse coordinate (x - 1/2) / 2), periodic in x, the wall rows' values held at the
+// walls; densities as they are, velocities halved (a coarse lattice velocity is twice
+// the fine one).  Each component keeps its mass: four times the coarse sum.
+__global__ void prolong_kernel(const float* __restrict__ cf, int ncx, int ncy, float* __restrict__ ff) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    const int nxf = 2 * ncx, nyf = 2 * ncy;
+    if (x >= nxf || y >= nyf) return;
+    // (x - 1/2) / 2 = X0 + t with t = 3/4 for even x, 1/4 for odd x
+    const int X0 = (x >> 1) - ((x & 1) ? 0 : 1), Y0 = (y >> 1) - ((y & 1) ? 0 : 1);
+    const float tx = (x & 1) ? 0.25f : 0.75f, ty = (y & 1) ? 0.25f : 0.75f;
+    const int xa = (X0 + ncx) % ncx, xb = (X0 + 1) % ncx;
+    const int ya = max(Y0, 0), yb = min(Y0 + 1, ncy - 1);
+    const size_t nc = (size_t)ncx * ncy, nf = (size_t)nxf * nyf;
+    for (int ch = 0; ch < 4; ++ch) {
+        const float* c = cf + (size_t)ch * nc;
+        const float v = (1.0f - ty) * ((1.0f - tx) * c[(size_t)ya * ncx + xa] + tx * c[(size_t)ya * ncx + xb]) +
+                        ty * ((1.0f - tx) * c[(size_t)yb * ncx + xa] + tx * c[(size_t)yb * ncx + xb]);
+        ff[(size_t)ch * nf + (size_t)y * nxf + x] = ch < 2 ? v : 0.5f * v;
+    }
+}
+
 // x = (raw - mean) / scale (network input); t = (target - raw) / out_scale (training target)
 __global__ void normalize_kernel(const float* __restrict__ raw, const float* __restrict__ target, size_t n,
                                  float4 mean, float4 scale, float4 oscale, float* __restrict__ x, float* __restrict__ t) {
@@ -673,6 +696,10 @@ struct lbm_closure {
     float *train_x = nullptr, *train_t = nullptr;
     int ntrain = 0;
     bool have_params = false;                                  // trained or set by the caller
+    float* snap = nullptr;                                     // [4 nc] coarse fields at the start of lbm_closure_run
+    float* fine_fld = nullptr;                                 // [4 nf] prolonged fields (fallback)
+    double* S_fine = nullptr;                                  // [18 nf] fine populations (fallback)
+    int64_t fallbacks = 0;                                     // intervals re-run on the fine solver
     float in_mean[4] = {0, 0, 0, 0}, in_scale[4] = {1, 1, 1, 1}, out_scale[4] = {1, 1, 1, 1};
 };
 
@@ -755,6 +782,31 @@ lbm_status cnn_check(lbm_closure* c) {
     return LBM_OK;
 }
 
+// The fallback: the fine plain solver re-runs `coarse_steps` coarse steps' worth of
+// time (four fine steps each) from the coarse fields saved in c->snap, prolonged to the
+// fine grid, and the coarse run restarts from the restriction of the result.
+lbm_status fine_fallback(lbm_closure* c, int64_t coarse_steps) {
+    const size_t nf = 4 * c->nc;
+    if (!c->fine_fld) {
+        if (cudaMalloc((void**)&c->fine_fld, 4 * nf * 4) != cudaSuccess) return cl_fail(LBM_ENOMEM, "fallback fields");
+        if (cudaMalloc((void**)&c->S_fine, 18 * nf * 8) != cudaSuccess) return cl_fail(LBM_ENOMEM, "fallback populations");
+    }
+    const dim3 grid((2 * c->ncx + 127) / 128, 2 * c->ncy);
+    lbm::prolong_kernel<<<grid, 128, 0, c->stream>>>(c->snap, c->ncx, c->ncy, c->fine_fld);
+    CL_TRY(cudaGetLastError(), "prolong");
+    lbm::fields_to_populations_kernel<<<512, 256, 0, c->stream>>>(c->fine_fld, nf, c->S_fine);
+    CL_TRY(cudaGetLastError(), "fine populations");
+    CL_TRY(lbm::handle_push_S(c->fine, c->S_fine), "push fine state");
+    CL_TRY(lbm::handle_clear_guard(c->fine), "clear fine guard");
+    CL_STATUS(lbm_step(c->fine, kFineStepsPerCoarse * coarse_steps));
+    CL_STATUS(lbm_sync(c->fine));
+    CL_STATUS(restrict_fine(c, c->raw));
+    CL_STATUS(set_coarse(c, c->raw));
+    CL_TRY(lbm::handle_clear_guard(c->coarse), "clear coarse guard");
+    ++c->fallbacks;
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -826,7 +878,8 @@ void lbm_closure_destroy(lbm_closure* c) {
     if (c->coarse) lbm_destroy(c->coarse);
     for (float* p : c->samp_raw) cudaFree(p);
     for (float* p : c->samp_tgt) cudaFree(p);
-    void* bufs[] = {c->params, c->grad, c->m, c->v, c->cnn_ws, c->raw, c->xin, c->yout, c->S, c->part, c->train_x, c->train_t};
+    void* bufs[] = {c->params, c->grad, c->m, c->v, c->cnn_ws, c->raw, c->xin, c->yout, c->S, c->part, c->train_x, c->train_t,
+                    c->snap, c->fine_fld, c->S_fine};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -893,6 +946,7 @@ lbm_status lbm_closure_create(const lbm_params* fine, int32_t interval, uint64_t
               cudaMalloc((void**)&c->xin, 4 * c->nc * 4) == cudaSuccess &&
               cudaMalloc((void**)&c->yout, 4 * c->nc * 4) == cudaSuccess &&
               cudaMalloc((void**)&c->S, 18 * c->nc * 8) == cudaSuccess &&
+              cudaMalloc((void**)&c->snap, 4 * c->nc * 4) == cudaSuccess &&
               cudaMalloc((void**)&c->part, kPartDoubles * 8) == cudaSuccess;
     if (!ok) return bail(LBM_ENOMEM, "closure buffers");
     c->net = lbm::cnn::carve(c->cnn_ws, c->ncx, c->ncy);
@@ -1057,6 +1111,35 @@ lbm_status lbm_closure_correct(lbm_closure* c, int32_t use_net) {
     if (!c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
     CL_STATUS(correct(c, use_net, true));
     return cnn_check(c);
+}
+
+lbm_status lbm_closure_run(lbm_closure* c, int64_t coarse_steps, lbm_diag* out) {
+    if (!c || coarse_steps < 0 || !out) return cl_fail(LBM_EINVAL, "invalid arguments");
+    if (!c->have_params) return cl_fail(LBM_ESTATE, "the network has not been trained");
+    constexpr int kRunMode = 4;
+    CL_STATUS(coarse_fields(c, c->snap));          // the state the fallback restarts from
+    const int64_t full = coarse_steps / c->interval, rest = coarse_steps % c->interval;
+    for (int64_t k = 0; k < full; ++k) {
+        CL_STATUS(lbm_step(c->coarse, c->interval));
+        CL_STATUS(correct(c, kRunMode, k == 0));
+    }
+    if (rest) CL_STATUS(lbm_step(c->coarse, rest));
+    // the indicators: the step kernels' guard (a NaN or negative density) and the
+    // tensor-core kernels' status (a wait that gave up)
+    lbm_status st = lbm_sync(c->coarse);
+    if (st == LBM_OK && full > 0) st = cnn_check(c);
+    if (st == LBM_EUNSTABLE || st == LBM_ETIMEOUT) {
+        CL_STATUS(fine_fallback(c, coarse_steps));
+    } else if (st != LBM_OK) {
+        return st;
+    }
+    return lbm_diagnostics(c->coarse, out);
+}
+
+lbm_status lbm_closure_fallbacks(lbm_closure* c, int64_t* count) {
+    if (!c || !count) return cl_fail(LBM_EINVAL, "NULL argument");
+    *count = c->fallbacks;
+    return LBM_OK;
 }
 
 lbm_status lbm_closure_params(lbm_closure* c, float* host, int32_t set) {

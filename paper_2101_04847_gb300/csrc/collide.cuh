@@ -53,6 +53,19 @@ __device__ __forceinline__ void velocity_and_accel(float2 rho, float2 jx, float2
     ay = fma2(splat(-ph.G), sy, make_float2(ph.ay_ext[0], ph.ay_ext[1]));
     if (y == 0) ay = add2(ay, make_float2(ph.ay_wall_bottom[0], ph.ay_wall_bottom[1]));
     if (y == ny - 1) ay = add2(ay, make_float2(ph.ay_wall_top[0], ph.ay_wall_top[1]));
+    if (ph.wall_mirror && (y == 0 || y == ny - 1)) {
+        // wall_mode 1: the virtual row beyond the wall holds this row's pseudopotentials
+        // (the kernels passed zeros for it).  Its three neighbours add w c psi: the
+        // straight one the other component's density here, the diagonals those at x + 1
+        // and x - 1, i.e. (1/9) psi' + (1/36)(E' + W') along the outward normal and
+        // (1/36)(E' - W') along x.
+        const float2 own = make_float2(rho.y, rho.x);
+        const float2 E = make_float2(psiB.E, psiA.E), W = make_float2(psiB.W, psiA.W);
+        const float2 dn = fma2(splat(1.0f / 9.0f), own, mul2(splat(1.0f / 36.0f), add2(E, W)));
+        const float2 dx = mul2(splat(1.0f / 36.0f), sub2(E, W));
+        ax = fma2(splat(-ph.G), dx, ax);
+        ay = fma2(splat(y == 0 ? ph.G : -ph.G), dn, ay);
+    }
 }
 
 // sum of nine values, associated as ((0+1)+(2+3)) + ((4+5)+(6+7)) + 8

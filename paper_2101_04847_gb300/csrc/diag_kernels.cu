@@ -100,6 +100,7 @@ struct DiagArgs {
     double* rowpart;    // [ny][nbx]: row partials of phi
     double* rowpart_c;  // [ny][nbx]: row partials of the mass fraction rho_A / (rho_A + rho_B)
     int nblocks, nbx;   // blocks in total / along x
+    int mirror;         // 1: the pseudopotential beyond a wall is the wall row's (wall_mode 1)
 };
 
 __device__ __forceinline__ int row_of(int r) { return blockIdx.y * BY + threadIdx.y + r * DY; }
@@ -135,8 +136,14 @@ __device__ __forceinline__ void block_sums(const dfl (&v)[N], const DiagArgs& a,
 __device__ __forceinline__ dfl at(const dfl* f, const DiagArgs& a, int x, int y) {
     return f[(size_t)y * a.nx + x];
 }
+// a density field's value as the Shan-Chen force sees it: beyond a wall 0, or with
+// the mirror the wall row's own value
 __device__ __forceinline__ dfl at0(const dfl* f, const DiagArgs& a, int x, int y) {
-    return (y < 0 || y >= a.ny) ? dfl{0.0f, 0.0f} : f[(size_t)y * a.nx + x];
+    if (y < 0 || y >= a.ny) {
+        if (!a.mirror) return dfl{0.0f, 0.0f};
+        y = y < 0 ? 0 : a.ny - 1;
+    }
+    return f[(size_t)y * a.nx + x];
 }
 
 // Exact sum of FP32 terms: every TwoSum error is kept in lo (its own rounding is
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(DX * DY) moments_kernel(const T* __restrict__ 
     block_sums<2>(v, a, T_MASS_A);
 }
 
-// sum_i w_i psi(x + c_i) c_i of a density field (zero on the virtual wall rows)
+// sum_i w_i psi(x + c_i) c_i of a density field (the virtual wall rows as at0 gives them)
 __device__ __forceinline__ void nbr_sum_d(const dfl* f, const DiagArgs& a, int x, int y, dfl& sx, dfl& sy) {
     const int xm = x == 0 ? a.nx - 1 : x - 1;
     const int xp = x == a.nx - 1 ? 0 : x + 1;
@@ -416,6 +423,7 @@ DiagArgs make_args(const DiagLaunch& D) {
     const double tm = D.tau_bar - 0.5;
     a.cK = dfl_of(kCs2 * kCs2 * tm * tm);
     a.floor_prod = dfl_of(1e-12);
+    a.mirror = D.wall_mirror;
     a.M = reinterpret_cast<dfl*>(D.scratch);
     a.U = reinterpret_cast<dfl*>(D.scratch + 4 * a.n);
     a.T = reinterpret_cast<dfl*>(D.scratch + 6 * a.n);
@@ -451,14 +459,22 @@ struct FeatArgs {
     size_t n;
     float G, gx, gw6[2], gext[2];
     float mean[4], scale[4];
+    int mirror;
 };
 
-// sum_i w_i rho(x + c_i) c_i of one density field, zero beyond the walls
+// sum_i w_i rho(x + c_i) c_i of one density field, zero beyond the walls (or the wall
+// rows' values with the mirror)
 __device__ __forceinline__ void nbr_sum_f(const float* __restrict__ r, const FeatArgs& a, int x, int y, float& sx,
                                           float& sy) {
     const int xm = x == 0 ? a.nx - 1 : x - 1;
     const int xp = x == a.nx - 1 ? 0 : x + 1;
-    auto at = [&](int xx, int yy) { return (yy < 0 || yy >= a.ny) ? 0.0f : r[(size_t)yy * a.nx + xx]; };
+    auto at = [&](int xx, int yy) {
+        if (yy < 0 || yy >= a.ny) {
+            if (!a.mirror) return 0.0f;
+            yy = yy < 0 ? 0 : a.ny - 1;
+        }
+        return r[(size_t)yy * a.nx + xx];
+    };
     const float E = at(xp, y), W = at(xm, y), N = at(x, y + 1), S = at(x, y - 1);
     const float d = at(xp, y + 1) - at(xm, y - 1);
     const float SE = at(xp, y - 1), NW = at(xm, y + 1);
@@ -503,6 +519,7 @@ cudaError_t launch_closure_features(const DiagLaunch& D, const float* rho2, cons
     a.n = (size_t)a.nx * a.ny;
     a.G = (float)D.G;
     a.gx = (float)D.gx;
+    a.mirror = D.wall_mirror;
     for (int s = 0; s < 2; ++s) {
         a.gw6[s] = (float)(D.G_wall[s] / 6.0);
         a.gext[s] = (float)D.g_ext[s];

@@ -125,6 +125,7 @@ lbm_status validate(const lbm_params* p) {
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->tile_x != 0 && p->tile_x != 128 && p->tile_x != 256) return fail(LBM_EINVAL, "tile_x must be 0, 128 or 256");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
+    if (p->wall_mode < 0 || p->wall_mode > 1) return fail(LBM_EINVAL, "wall_mode must be 0 or 1");
     const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
                            p->g, p->gx, p->amp, p->width, p->minority, p->y0, p->shift_A, p->shift_B};
     for (double v : vals)
@@ -206,6 +207,7 @@ lbm::DiagLaunch diag_launch(lbm_handle* h) {
     D.gx = p.gx;
     D.tau_bar = 0.5 * (p.tau_A + p.tau_B);
     D.crop = p.crop_rows;
+    D.wall_mirror = p.wall_mode == 1 ? 1 : 0;
     D.scratch = h->scratch();
     D.partials = (double*)(h->ws + h->L.partials);
     D.out = (double*)(h->ws + h->L.out);
@@ -348,6 +350,11 @@ lbm_status handle_reseed(lbm_handle* h, uint64_t seed) {
     h->p.seed = seed;
     destroy_graphs(h);
     return run_init(h);
+}
+cudaError_t handle_clear_guard(lbm_handle* h) {
+    h->unstable = false;
+    h->timed_out = false;
+    return cudaMemsetAsync(h->flag(), 0, sizeof(int), h->stream);
 }
 }  // namespace lbm
 
@@ -589,6 +596,7 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     ph.ay_ext[0] = (float)(-p->g);
     ph.ay_ext[1] = (float)(p->gravity_mode == 0 ? p->g : -p->g);
     ph.ax_ext = (float)p->gx;
+    ph.wall_mirror = p->wall_mode == 1 ? 1 : 0;
     ph.shift[0] = h->shift[0];
     ph.shift[1] = h->shift[1];
     // The instability guard rejects negative densities.  16-bit storage cannot hold a
@@ -656,6 +664,14 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
 lbm_status lbm_sync(lbm_handle* h) {
     if (!h) return fail(LBM_EINVAL, "handle is NULL");
     return check_flag(h);
+}
+
+lbm_status lbm_step_test_timeout(lbm_handle* h) {
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (h->in_ensemble) return fail(LBM_ESTATE, "ensemble members are stepped by their ensemble");
+    if (h->p.storage != LBM_STORE_F32) return fail(LBM_EINVAL, "the timeout test runs on FP32 storage");
+    LBM_TRY(lbm::launch_step_test_timeout(step_launch(h, h->cur), h->stream), "timeout test kernel");
+    return LBM_OK;
 }
 
 lbm_status lbm_step_count(lbm_handle* h, int64_t* step) {

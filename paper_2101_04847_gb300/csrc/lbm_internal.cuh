@@ -47,6 +47,7 @@ struct Physics {
     float ax_ext;      // body acceleration along x
     float shift[2];    // rho0_s of the shifted storage (0 for FP32)
     float rho_floor[2];  // smallest density the instability guard accepts (see lbm_create)
+    int wall_mirror;   // 1: the pseudopotential beyond a wall mirrors the wall row (wall_mode 1)
     // Time-step counter of the stochastic rounding: a launch reads *step_in and one of
     // its threads writes *step_in + 1 to *step_out, the counter the next launch reads
     // (two counters alternating with the buffers).  Null: no counter (seed 0).
@@ -129,12 +130,17 @@ struct PopView {
 };
 PopView handle_pops(lbm_handle* h);
 lbm_status handle_reseed(lbm_handle* h, uint64_t seed);
+// clear the guard flag (device word and the sticky host copies) after the state
+// has been replaced, queued on the handle's stream
+cudaError_t handle_clear_guard(lbm_handle* h);
 
 // message returned by lbm_last_error() on this thread (lbm_api.cu)
 void set_last_error(const std::string& msg);
 
 // step kernels (step_kernels.cu)
 cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st);
+// the block-staged FP32 step with its row copies withheld (tests of the timeout path)
+cudaError_t launch_step_test_timeout(const StepLaunch& L, cudaStream_t st);
 cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shift[2],
                         const double* y0, double mass_A, double mass_B, double minority,
                         double width, cudaStream_t st);
@@ -163,6 +169,7 @@ struct DiagLaunch {
     float shift[2];
     double G, G_wall[2], g_ext[2], gx, tau_bar;
     int crop;
+    int wall_mirror;     // pseudopotential beyond the walls: 0 none, 1 the wall rows' (wall_mode)
     double* scratch;     // 15 doubles per site
     double* partials;    // kDiagTerms * nblocks + 2 * ny * nbx
     double* out;         // kDiagTerms + 2 * ny doubles (terms, row sums of phi, of the mass fraction)

@@ -155,9 +155,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after kWaitLimit polls and raises bit 2 of the guard flag.
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+// Bounded wait: gives up after `limit` polls (kWaitLimit by default) and raises bit 2
+// of the guard flag.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* flag, uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return;
     atomicOr(flag, 2);
 }
@@ -579,8 +580,11 @@ typedef BlockRingT<kBlockTileW> BlockRing;
 
 // One block tile: columns [x0, x0 + TW) and rows [y0, y1) of one grid, TW threads.
 // dsm: the block_smem_bytes<T, TW>() of dynamic shared memory (row stages, then
-// the mbarriers).
-template <typename T, int TW = kBlockTileW>
+// the mbarriers).  kWithhold (the timeout test's instantiation only): no row copy is
+// issued and each wait gives up after kTestWaitLimit polls, so every wait of the tile
+// runs out with nothing in flight.
+constexpr uint32_t kTestWaitLimit = 4096;
+template <typename T, int TW = kBlockTileW, bool kWithhold = false>
 __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
                                            const Physics& ph, int x0, int y0, int y1, unsigned char* dsm,
                                            BlockRingT<TW>& sR, uint32_t seed, int* flag) {
@@ -612,6 +616,7 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     __syncthreads();
     int next = rfirst;  // next row to issue (every lane of warp 0 keeps the same count)
     auto issue = [&](int r) {   // warp 0, all lanes
+        if constexpr (kWithhold) return;
         const int j = (r - rfirst) % kBlockStages;
         uint64_t* b = &bar[j];
         if (t == 0) mbar_expect_tx(b, 18 * row_bytes);
@@ -624,7 +629,8 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
         for (; next <= rlast && next < rfirst + kBlockStages; ++next) issue(next);
     auto wait_row = [&](int r) {
         if (r >= rfirst && r <= rlast)
-            mbar_wait(&bar[(r - rfirst) % kBlockStages], (uint32_t)(((r - rfirst) / kBlockStages) & 1), flag);
+            mbar_wait(&bar[(r - rfirst) % kBlockStages], (uint32_t)(((r - rfirst) / kBlockStages) & 1), flag,
+                      kWithhold ? kTestWaitLimit : kWaitLimit);
     };
     auto stage_of = [&](int r) -> const T* {
         const int rr = min(max(r, rfirst), rlast);
@@ -727,6 +733,18 @@ step_block_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physi
     const uint32_t seed = launch_seed(ph);
     advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     block_tile<T, TW>(fin, fout, g, ph, blockIdx.x * TW, y0, y1, dsm, sR, seed, flag);
+}
+
+// The timeout test's kernel: step_block_kernel<float, 128> with the row copies withheld
+// (block_tile's kWithhold), so that every bounded wait gives up and raises bit 2 of the
+// guard.  Its output is garbage; the step counters are left alone.
+__global__ void __launch_bounds__(kBlockTileW, 512 / kBlockTileW)
+step_block_timeout_kernel(const float* __restrict__ fin, float* __restrict__ fout, Grid g, Physics ph, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ BlockRingT<kBlockTileW> sR;
+    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
+    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
+    block_tile<float, kBlockTileW, true>(fin, fout, g, ph, blockIdx.x * kBlockTileW, y0, y1, dsm, sR, 0u, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,6 +1077,24 @@ cudaError_t launch_step(const StepLaunch& L, int kernel, cudaStream_t st) {
         case LBM_STORE_BF16: return launch_step_t<__nv_bfloat16>(L, kernel, st);
         default: return launch_step_t<float>(L, kernel, st);
     }
+}
+
+cudaError_t launch_step_test_timeout(const StepLaunch& L, cudaStream_t st) {
+    if (L.storage != LBM_STORE_F32) return cudaErrorInvalidValue;
+    (void)cudaGetLastError();
+    const Grid& g = L.grid;
+    const size_t smem = block_smem_bytes<float, kBlockTileW>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(step_block_timeout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int gx = (g.nx + kBlockTileW - 1) / kBlockTileW;
+    dim3 grid(gx, std::max(1, std::min(g.ny / 8, 16)));
+    step_block_timeout_kernel<<<grid, kBlockTileW, smem, st>>>((const float*)L.fin, (float*)L.fout, g, L.phys, L.flag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(void* fout, const Grid& g, int storage, const float shift[2], const double* y0,

@@ -29,7 +29,7 @@ class LbmParams(C.Structure):
         ("amp", C.c_double), ("width", C.c_double), ("minority", C.c_double), ("y0", C.c_double),
         ("crop_rows", C.c_int32), ("storage", C.c_int32), ("kernel", C.c_int32), ("tile_y", C.c_int32),
         ("shift_A", C.c_double), ("shift_B", C.c_double),
-        ("tile_x", C.c_int32),
+        ("tile_x", C.c_int32), ("wall_mode", C.c_int32),
     ]
 
 
@@ -61,6 +61,7 @@ _PROTOS = {
     "lbm_step": (C.c_int, [_h, C.c_int64]),
     "lbm_sync": (C.c_int, [_h]),
     "lbm_step_count": (C.c_int, [_h, _P(C.c_int64)]),
+    "lbm_step_test_timeout": (C.c_int, [_h]),
     "lbm_diagnostics": (C.c_int, [_h, _P(LbmDiag)]),
     "lbm_diagnostics_async": (C.c_int, [_h]),
     "lbm_diagnostics_wait": (C.c_int, [_h, _P(LbmDiag)]),
@@ -105,6 +106,8 @@ _PROTOS = {
     "lbm_closure_normalisation": (C.c_int, [C.c_void_p, _P(C.c_float)]),
     "lbm_closure_set_normalisation": (C.c_int, [C.c_void_p, _P(C.c_float)]),
     "lbm_closure_correct": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_closure_run": (C.c_int, [C.c_void_p, C.c_int64, _P(LbmDiag)]),
+    "lbm_closure_fallbacks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "lbm_closure_solvers": (C.c_int, [C.c_void_p, _P(_h), _P(_h)]),
     "lbm_closure_destroy": (None, [C.c_void_p]),
 }
@@ -234,6 +237,11 @@ class Solver:
 
     def sync(self):
         _check(self.lib.lbm_sync(self._h), "lbm_sync")
+
+    def step_test_timeout(self):
+        """One step launch whose row copies are withheld: its bounded waits give up
+        (the timeout path's test; the state is left as it was)."""
+        _check(self.lib.lbm_step_test_timeout(self._h), "lbm_step_test_timeout")
 
     @property
     def step_count(self) -> int:
@@ -483,6 +491,19 @@ class Closure:
     def correct(self, use_net: int):
         """One correction of the coarse run's current state (no time steps)."""
         _check(self.lib.lbm_closure_correct(self._c, int(use_net)), "lbm_closure_correct")
+
+    def run(self, coarse_steps: int) -> dict:
+        """Production advance (mode 4 corrections, the fine solver as fallback); the
+        coarse run's diagnostics afterwards."""
+        d = LbmDiag()
+        _check(self.lib.lbm_closure_run(self._c, int(coarse_steps), C.byref(d)), "lbm_closure_run")
+        return diag_dict(d)
+
+    @property
+    def fallbacks(self) -> int:
+        n = C.c_int64()
+        _check(self.lib.lbm_closure_fallbacks(self._c, C.byref(n)), "lbm_closure_fallbacks")
+        return n.value
 
     def params(self) -> np.ndarray:
         out = np.empty(CNN_PARAMS, dtype=np.float32)

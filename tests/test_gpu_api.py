@@ -5,6 +5,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle import lbm_oracle as O
 from paper_2101_04847_gb300 import lbm
 from tests import inputs
 
@@ -179,3 +180,34 @@ def test_async_diagnostics_report_an_unstable_state(gpu):
         with pytest.raises(lbm.LbmError) as e:
             s.diagnostics_wait()
         assert e.value.status == lbm.LBM_EUNSTABLE
+
+
+def test_step_waits_that_run_out_report_a_timeout(gpu):
+    # failure detection without a GPU fault: a step launch whose row copies are
+    # withheld has every bounded wait give up (a few thousand polls each); the host
+    # reads LBM_ETIMEOUT, the context stays usable, and the state is untouched
+    nx, ny = 200, 48
+    d = inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=3)
+    f = inputs.as_float32(inputs.random_populations(17, nx, ny))
+    with lbm.Solver(kernel="staged", **d) as s:
+        s.set_populations(f)
+        s.step_test_timeout()
+        with pytest.raises(lbm.LbmError) as e:
+            s.sync()
+        assert e.value.status == lbm.LBM_ETIMEOUT
+        assert np.array_equal(s.populations(), f)
+        assert s.step_count == 0
+        with pytest.raises(lbm.LbmError) as e:
+            s.diagnostics()
+        assert e.value.status == lbm.LBM_ETIMEOUT          # sticky until a reset
+        s.reset()
+        s.set_populations(f)
+        s.step(1)
+        s.sync()
+        got = s.populations()
+    ref = O.step(f, O.Params(**{k: v for k, v in d.items() if k in O.Params.__dataclass_fields__}), 1)
+    assert np.max(np.abs(got - ref)) < 2e-6 * np.max(np.abs(ref))
+    with lbm.Solver(storage="f16", **d) as s16:
+        with pytest.raises(lbm.LbmError) as e:
+            s16.step_test_timeout()
+        assert e.value.status == lbm.LBM_EINVAL

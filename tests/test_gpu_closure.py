@@ -313,3 +313,90 @@ def test_normalisation_can_be_set_and_is_checked(gpu):
         assert c.normalisation()[5] == np.float32(0.25)      # a refused call changes nothing
     finally:
         c.close()
+
+
+def test_run_is_the_corrected_advance_then_the_diagnostics(gpu):
+    # lbm_closure_run(3 intervals + 4 steps) = lbm_closure_advance(3, 4), four more
+    # coarse steps and lbm_diagnostics of the coarse run, bit for bit
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        pc, f0, p32, norm = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(*norm)
+        _, co = c.solvers()
+        co.set_populations(f0.astype(np.float32))
+        d_run = c.run(34)
+        a = co.populations()
+        co.set_populations(f0.astype(np.float32))
+        c.advance(3, 4)
+        co.step(4)
+        d_ref = co.diagnostics()
+        b = co.populations()
+        assert c.fallbacks == 0
+        fresh = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+        with pytest.raises(lbm.LbmError):
+            fresh.run(10)                        # no trained or set parameters
+        fresh.close()
+    finally:
+        c.close()
+    assert np.array_equal(a, b)
+    for k in ("mass_A", "mass_B", "E_k", "E_p", "flux_pb", "flux_K", "flux_tau", "viscous", "h", "L_int"):
+        assert d_run[k] == d_ref[k], k
+
+
+def _prolong(fields):
+    """Fine fields from coarse ones: bilinear in the cell centres, periodic in x, the
+    wall rows held; velocities halved (fine lattice units)."""
+    out = []
+    for ch, a in enumerate(fields):
+        ny, nx = a.shape
+        xf = (np.arange(2 * nx) - 0.5) / 2.0
+        yf = (np.arange(2 * ny) - 0.5) / 2.0
+        x0 = np.floor(xf).astype(int)
+        y0 = np.floor(yf).astype(int)
+        tx, ty = xf - x0, yf - y0
+        xa, xb = x0 % nx, (x0 + 1) % nx
+        ya, yb = np.clip(y0, 0, ny - 1), np.clip(y0 + 1, 0, ny - 1)
+        v = ((1 - ty)[:, None] * ((1 - tx)[None, :] * a[np.ix_(ya, xa)] + tx[None, :] * a[np.ix_(ya, xb)])
+             + ty[:, None] * ((1 - tx)[None, :] * a[np.ix_(yb, xa)] + tx[None, :] * a[np.ix_(yb, xb)]))
+        out.append(v if ch < 2 else 0.5 * v)
+    return out
+
+
+def test_run_falls_back_to_the_fine_solver(gpu):
+    # velocity corrections ten thousand times too large drive the corrected coarse run
+    # unstable; the call then re-runs its time on the fine plain solver from the saved
+    # coarse fields and restarts the coarse run from the restriction of the result
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        pc, f0, p32, (mean, scale, oscale) = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(mean, scale, np.array([3e-3, 3e-3, 40.0, 40.0], dtype=np.float32))
+        _, co = c.solvers()
+        co.set_populations(f0.astype(np.float32))
+        start = co.fields()
+        d = c.run(20)
+        assert c.fallbacks == 1
+        got = co.populations()
+    finally:
+        c.close()
+    assert np.isfinite(d["E_k"]) and d["status"] == lbm.LBM_OK
+    # the same fallback on the host side of the ABI: prolongation of the saved fields
+    # (FP32, as saved), equilibrium fine populations, 80 steps of a plain fine solver,
+    # 2 x 2 block means (densities averaged, velocity momentum-weighted, coarse units)
+    fa, fb, fux, fuy = _prolong([start[k].astype(np.float32).astype(np.float64) for k in ("rhoA", "rhoB", "ux", "uy")])
+    with lbm.Solver(lbm.default_params(**FINE)) as fine:
+        fine.set_populations(np.stack([O.equilibrium(fa, fux, fuy), O.equilibrium(fb, fux, fuy)]))
+        fine.step(80)
+        ff = fine.fields()
+    blk = lambda a: a.reshape(a.shape[0] // 2, 2, a.shape[1] // 2, 2).sum(axis=(1, 3))
+    rho = ff["rhoA"] + ff["rhoB"]
+    rA, rB = blk(ff["rhoA"]) / 4, blk(ff["rhoB"]) / 4
+    ux = 2 * blk(rho * ff["ux"]) / blk(rho)
+    uy = 2 * blk(rho * ff["uy"]) / blk(rho)
+    ref = np.stack([O.equilibrium(rA, ux, uy), O.equilibrium(rB, ux, uy)])
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # each component's mass survives the round trip (the restriction and the
+    # prolongation keep it; the fine steps conserve it)
+    for s, k in ((0, "rhoA"), (1, "rhoB")):
+        assert abs(got[s].sum() - start[k].sum()) <= 1e-5 * start[k].sum()

@@ -1,8 +1,9 @@
 """Parity of the CUDA diagnostics and field extraction with the oracle (GPU).
 
-Both sides evaluate the per-site terms in FP64 from the same FP32-rounded
-populations; only the order of the FP64 sums differs, so the terms agree to
-~1e-9 of their scale and the crossing counts exactly.
+Both sides evaluate the per-site terms from the same FP32-rounded populations:
+the oracle in FP64, the GPU in double-float arithmetic (pairs of FP32 values,
+about 44 significant bits) with FP64 block sums; the terms agree to ~1e-9 of
+their scale and the crossing counts exactly.
 """
 import numpy as np
 import pytest
@@ -37,10 +38,11 @@ def check_diag(got, ref, rtol=1e-9):
     assert abs(got["L_int"] - ref["L_int"]) <= 1e-12 * ref["L_int"]
 
 
-@pytest.mark.parametrize("nx,ny,G,steps", [(96, 80, 1.4, 300), (100, 70, 0.0, 150), (33, 64, 1.4, 40)])
-def test_diagnostics_match_the_oracle(gpu, nx, ny, G, steps):
+@pytest.mark.parametrize("nx,ny,G,steps,wall_mode", [(96, 80, 1.4, 300, 0), (100, 70, 0.0, 150, 0), (33, 64, 1.4, 40, 0),
+                                                  (96, 80, 1.4, 300, 1)])
+def test_diagnostics_match_the_oracle(gpu, nx, ny, G, steps, wall_mode):
     d = inputs.params(inputs.C0, nx=nx, ny=ny, G=G, g=1e-4, amp=4.0,
-                      minority=0.0 if G == 0.0 else 0.08, crop_rows=6)
+                      minority=0.0 if G == 0.0 else 0.08, crop_rows=6, wall_mode=wall_mode)
     f, p = evolved_state(d, steps)
     ref = O.diagnostics(f, p)
     with lbm.Solver(**d) as s:
@@ -51,8 +53,9 @@ def test_diagnostics_match_the_oracle(gpu, nx, ny, G, steps):
     assert np.max(np.abs(rows - ref["phi_rows"])) <= 1e-12
 
 
-def test_fields_match_the_oracle(gpu):
-    d = inputs.params(inputs.C0, nx=70, ny=50, g=1e-4, G_wall_A=0.2, crop_rows=5)
+@pytest.mark.parametrize("wall_mode", [0, 1])
+def test_fields_match_the_oracle(gpu, wall_mode):
+    d = inputs.params(inputs.C0, nx=70, ny=50, g=1e-4, G_wall_A=0.2, crop_rows=5, wall_mode=wall_mode)
     f, p = evolved_state(d, 100)
     ref = O.fields(f, p)
     with lbm.Solver(**d) as s:

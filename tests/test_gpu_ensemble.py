@@ -1,13 +1,16 @@
 """Ensemble launch and the tile tuner (GPU).
 
 Every member of an ensemble advanced by the one-launch-per-step kernel must
-match the same realisation advanced alone by the block-staged kernel (the same
-tile code, compiled into another kernel, so equal up to FMA contraction), and
-tuning must leave states untouched.
+match the FP64 oracle (FP32 members within the 1e-5 density contract, every
+member within the one-step rounding bound of its storage), and the same
+realisation advanced alone by the block-staged kernel (the same tile code,
+compiled into another kernel, so equal up to FMA contraction); tuning must leave
+states untouched.
 """
 import numpy as np
 import pytest
 
+from oracle import lbm_oracle as O
 from paper_2101_04847_gb300 import lbm
 from tests import inputs
 
@@ -89,3 +92,66 @@ def test_tune_keeps_state_and_caches(gpu, tmp_path):
         ty2, ms2 = s2.tune(cache)                                      # found in the cache, not re-timed
         assert ty2 == ty and ms2 == pytest.approx(ms, rel=1e-3)   # stored with 6 decimals
         assert s2.get_params().tile_x == tx
+
+
+def oracle_params(m):
+    d = inputs.params(inputs.C0, crop_rows=5, g=1e-4)
+    d.update(m)
+    return O.Params(**{k: v for k, v in d.items() if k in O.Params.__dataclass_fields__})
+
+
+# mixed grids, couplings and storage types; uneven grids with ragged tile tails
+ORACLE_MEMBERS = [
+    dict(nx=256, ny=128, G=1.4, seed=1, storage="f32"),
+    dict(nx=97, ny=200, G=0.0, minority=0.0, seed=2, storage="f32"),
+    dict(nx=150, ny=66, G=1.2, seed=5, storage="f32"),
+    dict(nx=160, ny=64, G=1.2, seed=3, storage="f16"),
+    dict(nx=300, ny=90, G=1.4, seed=4, storage="bf16"),
+]
+
+
+@pytest.mark.parametrize("tile_y", [16, 1])
+def test_ensemble_fp32_members_match_the_oracle(gpu, tile_y):
+    # every FP32 member, advanced from its initial state through one 50-step graph and
+    # 23 single launches of the ensemble kernel, against the FP64 oracle's own run
+    params = [member_params(m, tile_y=tile_y) for m in ORACLE_MEMBERS]
+    with lbm.Ensemble(params) as ens:
+        ens.step(73)
+        ens.sync()
+        got = [m.fields() for m in ens.members]
+    for m, g in zip(ORACLE_MEMBERS, got):
+        if m["storage"] != "f32":
+            continue
+        p = oracle_params(m)
+        ref = O.fields(O.step(O.initial_populations(p), p, 73), p)
+        for k in ("rhoA", "rhoB"):
+            err = float(np.max(np.abs(g[k] - ref[k])) / np.max(np.abs(ref[k])))
+            assert err <= 1e-5, (m, k, err)
+
+
+@pytest.mark.parametrize("tile_y", [16, 1])
+def test_ensemble_one_step_from_set_states_matches_the_oracle(gpu, tile_y):
+    # each member set to seeded random populations (as its storage holds them), one
+    # ensemble step, against one oracle step from the state read back: FP32 to the
+    # arithmetic's rounding, 16-bit within one spacing of the stored mantissa
+    # (stochastic rounding of the stores), as for the solo kernels
+    params = [member_params(m, tile_y=tile_y) for m in ORACLE_MEMBERS]
+    with lbm.Ensemble(params) as ens:
+        start = []
+        for k, mem in enumerate(ens.members):
+            mem.set_populations(inputs.random_populations(40 + k, mem.nx, mem.ny, lo=0.02, hi=0.2))
+            start.append(mem.populations())
+        ens.step(1)
+        ens.sync()
+        got = [mem.populations() for mem in ens.members]
+    for m, f, g in zip(ORACLE_MEMBERS, start, got):
+        p = oracle_params(m)
+        ref = O.step(f, p, 1)
+        if m["storage"] == "f32":
+            allowed = 2e-6 * np.max(np.abs(ref))
+        else:
+            rho0 = [p.mass_A * (1 + p.minority) / 2, p.mass_B * (1 + p.minority) / 2]
+            h = ref - np.array(rho0)[:, None, None, None] * O.W[None, :, None, None]
+            bits = {"f16": 10, "bf16": 7}[m["storage"]]
+            allowed = 2.0 ** -bits * np.max(np.abs(h)) + 1e-6 * np.max(np.abs(ref))
+        assert float(np.max(np.abs(g - ref))) <= allowed, m

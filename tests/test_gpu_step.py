@@ -88,6 +88,8 @@ def test_tile_widths_give_identical_states(gpu, storage):
     dict(gravity_mode=1, g=3e-4, gx=2e-4),            # same-sign gravity and an x body force
     dict(tau_A=0.7, tau_B=1.3, G=0.9),                # unequal relaxation times
     dict(G=0.0, g=0.0),                               # no force at all
+    dict(wall_mode=1),                                # pseudopotential mirrored across the walls
+    dict(wall_mode=1, G_wall_A=0.3, G_wall_B=-0.2, tau_A=0.7, tau_B=1.3),
 ])
 def test_one_step_force_variants(gpu, kernel, extra):
     nx, ny = 96, 40
@@ -122,6 +124,19 @@ def test_small_configuration_1000_steps(gpu, kernel, c0_oracle_1000):
     # the velocity is small (~1e-3 of c): compare against its own scale
     for k in ("ux", "uy"):
         assert np.max(np.abs(got[k] - ref[k])) <= 1e-3 * np.max(np.abs(ref["ux"]) + np.abs(ref["uy"])), k
+
+
+def test_mirror_walls_1000_steps(gpu):
+    # wall_mode 1 (the pseudopotential of the wall rows mirrored across the walls) on
+    # the small configuration: the same 1e-5 contract on each density after 1000 steps
+    d = inputs.params(inputs.C0, seed=2, wall_mode=1)
+    p = oracle_params(d)
+    ref = O.fields(O.step(O.initial_populations(p), p, 1000), p)
+    with lbm.Solver(kernel="staged", **d) as s:
+        s.step(1000)
+        got = s.fields()
+    for k in ("rhoA", "rhoB"):
+        assert rel_err(got[k], ref[k]) <= 1e-5, k
 
 
 def test_miscible_variant_200_steps(gpu):
