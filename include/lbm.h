@@ -50,8 +50,10 @@ typedef enum {
     LBM_EINVAL = 1,     /* invalid argument or parameter set */
     LBM_ENOMEM = 2,     /* allocation failed or workspace too small */
     LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
-    LBM_EUNSTABLE = 4,  /* sticky: a NaN or negative density was seen by the step (with 16-bit
-                         * storage: below -1 % (FP16) or -5 % (BF16) of the shift rho0_s) */
+    LBM_EUNSTABLE = 4,  /* sticky: a NaN or a negative density was seen by the step: below
+                         * -0.1 % (FP32), -1 % (FP16) or -5 % (BF16) of rho0_s =
+                         * mass_s (1 + minority) / 2, which leaves room for the rounding-level
+                         * values of an absent component */
     LBM_ETIMEOUT = 5,   /* sticky: a bounded device-side wait gave up */
     LBM_ESTATE = 6,     /* call not valid in the handle's current state */
     LBM_EIO = 7         /* file I/O error (save/load) */
@@ -69,7 +71,9 @@ typedef enum {
     LBM_KERNEL_STAGED = 2,   /* fused kernel, rows staged in shared memory by bulk async copies,
                               * block-wide sweep (the default: the fastest; the ensemble's tile code) */
     LBM_KERNEL_WARP = 3,     /* as STAGED, one independent sweep per warp */
-    LBM_KERNEL_PIPE = 4      /* as STAGED, warps sweep independently over shared stages (no block barrier) */
+    LBM_KERNEL_PIPE = 4,     /* as STAGED, warps sweep independently over shared stages (no block barrier) */
+    LBM_KERNEL_DECOUPLED = 5 /* as STAGED (same tiles and row stages), but no block barrier per row: each warp
+                              * keeps its own density ring, stages are handed back through per-stage barriers */
 } lbm_kernel;
 
 /* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
@@ -104,6 +108,9 @@ typedef struct {
                               * leaves it open): 0 = none (psi = 0 on the virtual rows y = -1 and
                               * y = ny); 1 = mirror (those rows hold the wall rows' own psi: a
                               * neutral wall that exerts no force on a uniform fluid) */
+    int32_t x_offset;        /* the grid is columns [x_offset, x_offset + nx) of a whole grid of */
+    int32_t nx_total;        /* nx_total columns (domain decomposition along x): the initial
+                              * interface follows the whole grid; nx_total 0 = nx (x_offset 0) */
 } lbm_params;
 
 /* Diagnostics of one state (Section 3).  Averages <.> run over the sub-domain
@@ -184,6 +191,25 @@ lbm_status lbm_step_count(lbm_handle* h, int64_t* step);
  * lbm_diagnostics returns LBM_ETIMEOUT, which stays raised until lbm_reset.
  * FP32 storage only (else LBM_EINVAL); asynchronous. */
 lbm_status lbm_step_test_timeout(lbm_handle* h);
+
+/* Domain decomposition along x (an extension of the paper's single-grid runs): a
+ * grid split into sub-grids of consecutive columns, one solver each (x_offset and
+ * nx_total of lbm_params place a sub-grid in the whole grid), advances one step at
+ * a time, and between steps every sub-grid's ghost columns take its neighbours' edge
+ * columns.  The block-staged and decoupled kernels read the stored populations of
+ * the two columns beside the grid from those ghost columns, so the split run equals
+ * the whole-grid run bit for bit; the other kernels wrap x inside each solver and
+ * cannot be split.  lbm_halo_pack copies the two edge columns of the current state
+ * (side 0: columns 0, 1; side 1: nx - 2, nx - 1) to dev_buf, lbm_halo_unpack copies
+ * dev_buf into the ghost columns (side 0: -2, -1 from the left neighbour's side-1
+ * pack; side 1: nx, nx + 1 from the right neighbour's side-0 pack).  dev_buf: device
+ * memory of lbm_halo_bytes bytes (36 * ny stored values, [plane][row][column]),
+ * owned by the caller.  Both are queued on the solver's stream; side other than 0
+ * or 1 gives LBM_EINVAL.  The diagnostics of a sub-grid treat it as periodic in x
+ * (their derivatives at its two edges wrap inside it). */
+lbm_status lbm_halo_bytes(lbm_handle* h, size_t* bytes);
+lbm_status lbm_halo_pack(lbm_handle* h, int32_t side, void* dev_buf);
+lbm_status lbm_halo_unpack(lbm_handle* h, int32_t side, const void* dev_buf);
 
 /* Diagnostics of the current state (Section 3); synchronises.  *out is filled
  * even when the returned status is LBM_EUNSTABLE. */

@@ -888,7 +888,8 @@ void lbm_closure_destroy(lbm_closure* c) {
 
 lbm_status lbm_closure_coarse_params(const lbm_params* fine, lbm_params* out) {
     if (!fine || !out) return cl_fail(LBM_EINVAL, "NULL argument");
-    if (fine->nx % 2 || fine->ny % 2) return cl_fail(LBM_EINVAL, "the fine grid must have even nx and ny");
+    if (fine->nx % 2 || fine->ny % 2 || fine->x_offset % 2 || fine->nx_total % 2)
+        return cl_fail(LBM_EINVAL, "the fine grid must have even nx, ny, x_offset and nx_total");
     lbm_params p = *fine;
     p.nx = fine->nx / 2;
     p.ny = fine->ny / 2;
@@ -898,6 +899,8 @@ lbm_status lbm_closure_coarse_params(const lbm_params* fine, lbm_params* out) {
     p.width = std::max(0.5, fine->width / 2.0);
     p.y0 = fine->y0 < 0.0 ? -1.0 : fine->y0 / 2.0;
     p.crop_rows = std::max(3, fine->crop_rows / 2);
+    p.x_offset = fine->x_offset / 2;
+    p.nx_total = fine->nx_total / 2;
     p.storage = LBM_STORE_F32;
     p.kernel = LBM_KERNEL_STAGED;
     p.tile_y = 0;

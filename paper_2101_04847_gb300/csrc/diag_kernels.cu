@@ -167,10 +167,10 @@ __global__ void __launch_bounds__(DX * DY) moments_kernel(const T* __restrict__ 
         const int y = row_of(r);
         if (x >= a.nx || y >= a.ny) break;
         const float shift[2] = {sA, sB};
-        const int xm = x == 0 ? a.nx - 1 : x - 1;
-        const int xp = x == a.nx - 1 ? 0 : x + 1;
+        // the columns beside the grid from the ghost columns (periodic copies, or a
+        // split grid's neighbours)
         float f[2][9];
-        pull_site<T>(fin, a.g, shift, y, x, xm, xp, f);
+        pull_site<T>(fin, a.g, shift, y, x, x - 1, x + 1, f);
         dfl rho[2], jx[2], jy[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {

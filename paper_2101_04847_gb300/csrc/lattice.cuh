@@ -125,7 +125,9 @@ __device__ __forceinline__ void store_site_sr(T* __restrict__ fout, const Grid& 
                                               const float h[2][9], uint32_t seed) {
     T* q = fout + (size_t)y * g.pitch + g.origin + x;
     T tv[2][9];
-    const uint32_t site = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+    // the site's index in the whole grid, so that a split grid draws the same bits
+    const uint32_t site = g.nx_total > 0 ? (uint32_t)y * (uint32_t)g.nx_total + (uint32_t)(g.x_offset + x)
+                                         : (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         uint32_t r = hash_lowbias32((site * 2u + (uint32_t)s) ^ seed);

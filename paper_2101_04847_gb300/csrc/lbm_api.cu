@@ -53,25 +53,33 @@ double unit_double(uint64_t v) { return (double)(v >> 11) * (1.0 / 9007199254740
 
 // Interface height y0(x) = base + amp * eta(x) / max|eta|,
 // eta(x) = sum_{m=1..M} a_m sin(2 pi m x / nx + theta_m), draws a_1, theta_1, a_2, ...
+// Interface heights y0(x) for the handle's columns x = -1 .. nx (index x + 1): the
+// columns beside the grid too, which the initial state's streamed-in populations come
+// from.  Column x is column x_offset + x of the whole grid of nx_total columns
+// (periodic), so the sub-grids of a split grid start from the whole grid's state;
+// the normalisation uses the whole grid's largest deflection.
 std::vector<double> interface_height(const lbm_params& p) {
     const double two_pi = 6.283185307179586476925286766559;
+    const int total = p.nx_total > 0 ? p.nx_total : p.nx;
     std::vector<double> a(p.n_modes), th(p.n_modes);
     uint64_t st = p.seed;
     for (int m = 0; m < p.n_modes; ++m) {
         a[m] = unit_double(splitmix64_next(st));
         th[m] = two_pi * unit_double(splitmix64_next(st));
     }
-    std::vector<double> eta(p.nx, 0.0);
-    double peak = 0.0;
-    for (int x = 0; x < p.nx; ++x) {
+    auto eta_at = [&](int xg) {
         double e = 0.0;
-        for (int m = 0; m < p.n_modes; ++m) e += a[m] * std::sin(two_pi * (m + 1) * x / p.nx + th[m]);
-        eta[x] = e;
-        peak = std::fmax(peak, std::fabs(e));
-    }
+        for (int m = 0; m < p.n_modes; ++m) e += a[m] * std::sin(two_pi * (m + 1) * xg / total + th[m]);
+        return e;
+    };
+    double peak = 0.0;
+    for (int xg = 0; xg < total; ++xg) peak = std::fmax(peak, std::fabs(eta_at(xg)));
     const double base = p.y0 < 0.0 ? p.ny / 2.0 : p.y0;
-    std::vector<double> y0(p.nx);
-    for (int x = 0; x < p.nx; ++x) y0[x] = peak > 0.0 ? base + p.amp * eta[x] / peak : base;
+    std::vector<double> y0(p.nx + 2);
+    for (int x = -1; x <= p.nx; ++x) {
+        const int xg = ((x + p.x_offset) % total + total) % total;
+        y0[x + 1] = peak > 0.0 ? base + p.amp * eta_at(xg) / peak : base;
+    }
     return y0;
 }
 
@@ -105,7 +113,7 @@ Layout make_layout(const lbm_params& p) {
     L.partials = off; off = align_up(off + lbm::diag_partials_doubles(p.nx, p.ny) * sizeof(double));
     L.out = off; off = align_up(off + (lbm::kDiagTerms + 2 * (size_t)p.ny) * sizeof(double));
     L.flag = off; off = align_up(off + 16);
-    L.y0 = off; off = align_up(off + (size_t)p.nx * sizeof(double));
+    L.y0 = off; off = align_up(off + (size_t)(p.nx + 2) * sizeof(double));
     L.total = off;
     return L;
 }
@@ -121,11 +129,14 @@ lbm_status validate(const lbm_params* p) {
     if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
     if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny");
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
-    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_PIPE) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_DECOUPLED) return fail(LBM_EINVAL, "unknown kernel");
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->tile_x != 0 && p->tile_x != 128 && p->tile_x != 256) return fail(LBM_EINVAL, "tile_x must be 0, 128 or 256");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
     if (p->wall_mode < 0 || p->wall_mode > 1) return fail(LBM_EINVAL, "wall_mode must be 0 or 1");
+    if (p->x_offset < 0 || p->nx_total < 0 || (p->nx_total > 0 && (int64_t)p->x_offset + p->nx > p->nx_total) ||
+        (p->nx_total == 0 && p->x_offset != 0))
+        return fail(LBM_EINVAL, "x_offset and nx_total must place the grid inside a whole grid of nx_total columns");
     const double vals[] = {p->tau_A, p->tau_B, p->G, p->G_wall_A, p->G_wall_B, p->mass_A, p->mass_B,
                            p->g, p->gx, p->amp, p->width, p->minority, p->y0, p->shift_A, p->shift_B};
     for (double v : vals)
@@ -415,7 +426,7 @@ extern "C" lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* t
         const int cand[] = {0, 8, 12, 16, 24, 32, 48, 64, 96, 128};   // 0: the kernel's own default
         // tile widths: the block-staged kernel has two; the others ignore tile_x
         const int xs_staged[] = {lbm::kBlockTileW, lbm::kWideTileW}, xs_other[] = {0};
-        const bool staged = h->p.kernel == LBM_KERNEL_STAGED;
+        const bool staged = h->p.kernel == LBM_KERNEL_STAGED || h->p.kernel == LBM_KERNEL_DECOUPLED;
         const int* xs = staged ? xs_staged : xs_other;
         const int nxs = staged ? 2 : 1;
         cudaEvent_t a, b;
@@ -577,6 +588,8 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     h->grid.pitch = L.pitch;
     h->grid.origin = L.origin;
     h->grid.plane = L.plane;
+    h->grid.x_offset = p->x_offset;
+    h->grid.nx_total = p->nx_total;
     const bool shifted = p->storage != LBM_STORE_F32;
     const double sA = p->shift_A > 0.0 ? p->shift_A : 0.5 * p->mass_A * (1.0 + p->minority);
     const double sB = p->shift_B > 0.0 ? p->shift_B : 0.5 * p->mass_B * (1.0 + p->minority);
@@ -599,14 +612,18 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     ph.wall_mirror = p->wall_mode == 1 ? 1 : 0;
     ph.shift[0] = h->shift[0];
     ph.shift[1] = h->shift[1];
-    // The instability guard rejects negative densities.  16-bit storage cannot hold a
-    // pure phase exactly (h = -w rho0 is not on its grid), and its stochastic rounding
-    // makes the density of an absent component fluctuate around zero by a few units
-    // of the stored spacing: there the guard accepts down to -1 % (FP16) or -5 %
-    // (BF16) of rho0_s, far above the rounding noise and far below a real blow-up.
-    const float floor_frac = p->storage == LBM_STORE_F16 ? 0.01f : (p->storage == LBM_STORE_BF16 ? 0.05f : 0.0f);
-    ph.rho_floor[0] = -floor_frac * h->shift[0];
-    ph.rho_floor[1] = -floor_frac * h->shift[1];
+    // The instability guard rejects negative densities.  A component absent from a
+    // phase (minority 0) has density 0 there, and near a front the over-relaxation of
+    // tau < 1 sends it a few rounding units below zero (1e-17 at tau = 0.53 in FP32).
+    // 16-bit storage cannot hold a pure phase exactly (h = -w rho0 is not on its
+    // grid), and its stochastic rounding makes the density of an absent component
+    // fluctuate around zero by a few units of the stored spacing.  So the guard
+    // accepts down to -0.1 % (FP32), -1 % (FP16) or -5 % (BF16) of
+    // rho0_s = mass_s (1 + minority) / 2, far above the rounding noise and far below
+    // a real blow-up.
+    const float floor_frac = p->storage == LBM_STORE_F16 ? 0.01f : (p->storage == LBM_STORE_BF16 ? 0.05f : 0.001f);
+    ph.rho_floor[0] = (float)(-floor_frac * sA);
+    ph.rho_floor[1] = (float)(-floor_frac * sB);
     ph.step_in = nullptr;    // set per launch (step_launch)
     ph.step_out = nullptr;
     st = run_init(h);

@@ -62,6 +62,8 @@ struct Grid {
     int origin;         // element offset of column 0 in a row (128 bytes); columns
                         // -2, -1, nx, nx+1 hold periodic copies of nx-2, nx-1, 0, 1
     size_t plane;       // elements per (component, direction) plane = ny * pitch
+    int x_offset = 0;   // column 0 is column x_offset of a whole grid of nx_total columns
+    int nx_total = 0;   // (domain decomposition; 0 = nx): the stochastic rounding's site index
 };
 
 // Columns of one block tile of the block-staged kernel (one thread per column): the

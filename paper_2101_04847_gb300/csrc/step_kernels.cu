@@ -615,13 +615,30 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     }
     __syncthreads();
     int next = rfirst;  // next row to issue (every lane of warp 0 keeps the same count)
+    // Planes of row r the tile reads (bit p: plane p = 9 s + i).  The tile's own rows
+    // and the wall rows (bounce-back reads the opposite planes) take all 18; of the
+    // halo rows only the populations that stream into the tile or into the density
+    // rows y0 - 1 and y1: c_y = +1 from y0 - 2, c_y = 0 or +1 from y0 - 1, c_y = 0 or
+    // -1 from y1, c_y = -1 from y1 + 1 (directions 2, 5, 6 move up, 4, 7, 8 down).
+    auto planes_of = [&](int r) -> uint32_t {
+        constexpr uint32_t both = 1u | (1u << 9);
+        constexpr uint32_t up = ((1u << 2) | (1u << 5) | (1u << 6)) * both;
+        constexpr uint32_t mid = ((1u << 0) | (1u << 1) | (1u << 3)) * both;
+        constexpr uint32_t down = ((1u << 4) | (1u << 7) | (1u << 8)) * both;
+        if ((r >= y0 && r < y1) || r == 0 || r == g.ny - 1) return up | mid | down;
+        if (r == y0 - 2) return up;
+        if (r == y0 - 1) return up | mid;
+        if (r == y1) return mid | down;
+        return down;   // y1 + 1
+    };
     auto issue = [&](int r) {   // warp 0, all lanes
         if constexpr (kWithhold) return;
         const int j = (r - rfirst) % kBlockStages;
         uint64_t* b = &bar[j];
-        if (t == 0) mbar_expect_tx(b, 18 * row_bytes);
+        const uint32_t planes = planes_of(r);
+        if (t == 0) mbar_expect_tx(b, (uint32_t)__popc(planes) * row_bytes);
         __syncwarp();
-        if (t < 18)
+        if (t < 18 && ((planes >> t) & 1u))
             bulk_copy_g2s(stage + (size_t)j * 18 * W + t * W, win + (size_t)r * g.pitch + (size_t)t * g.plane,
                           row_bytes, b);
     };
@@ -719,6 +736,227 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
         row(y, fa, fb);
         if (y + 1 < y1) row(y + 1, fb, fa);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled block tile (LBM_KERNEL_DECOUPLED).  The row stages, pulls and
+// collision of block_tile without its block barrier per row: each warp keeps the
+// densities of its own 32 columns, and of the two columns beside them (lanes 0 and
+// 31 pull those as well), in a density ring of its own, and a stage is handed back
+// through an "empty" mbarrier on which each warp arrives once it no longer reads
+// the stage's row.  A warp waits only for the rows it reads (full barriers); warp
+// 0, whose lanes 0-17 issue the copies, also waits until every warp has handed back
+// the stage it refills.  Stage indices and barrier phases advance incrementally,
+// without a division by the stage count.
+// ---------------------------------------------------------------------------
+template <typename T, int TW> struct DecCfg { static constexpr int kStages = 5; };
+template <> struct DecCfg<__half, kWideTileW> { static constexpr int kStages = 8; };
+template <> struct DecCfg<__nv_bfloat16, kWideTileW> { static constexpr int kStages = 8; };
+
+template <typename T, int TW>
+size_t dec_smem_bytes() {
+    return (size_t)DecCfg<T, TW>::kStages * (18 * BlockWin<T, TW>::value * sizeof(T) + 2 * sizeof(uint64_t));
+}
+template <int TW> using DecRingT = float[TW / 32][4][2][34];
+
+// Planes of row r that the tile [y0, y1) reads (bit p: plane p = 9 s + i): all 18 for
+// its own rows and the wall rows (bounce-back reads the opposite planes); of the halo
+// rows only the populations that stream into the tile or into the density rows y0 - 1
+// and y1: c_y = +1 from y0 - 2, c_y = 0 or +1 from y0 - 1, c_y = 0 or -1 from y1 and
+// c_y = -1 from y1 + 1 (directions 2, 5, 6 move up, 4, 7, 8 down).
+__device__ __forceinline__ uint32_t tile_row_planes(int r, int y0, int y1, int ny) {
+    constexpr uint32_t both = 1u | (1u << 9);
+    constexpr uint32_t up = ((1u << 2) | (1u << 5) | (1u << 6)) * both;
+    constexpr uint32_t mid = ((1u << 0) | (1u << 1) | (1u << 3)) * both;
+    constexpr uint32_t down = ((1u << 4) | (1u << 7) | (1u << 8)) * both;
+    if ((r >= y0 && r < y1) || r == 0 || r == ny - 1) return up | mid | down;
+    if (r == y0 - 2) return up;
+    if (r == y0 - 1) return up | mid;
+    if (r == y1) return mid | down;
+    return down;   // y1 + 1
+}
+
+template <typename T, int TW>
+__device__ __forceinline__ void dec_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
+                                         const Physics& ph, int x0, int y0, int y1, unsigned char* dsm,
+                                         DecRingT<TW>& sR, uint32_t seed, int* flag) {
+    constexpr int W = BlockWin<T, TW>::value;
+    constexpr int kAlign = BlockWin<T, TW>::kAlign;
+    constexpr int S = DecCfg<T, TW>::kStages;
+    constexpr int NW = TW / 32;
+    T* stage = reinterpret_cast<T*>(dsm);
+    uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)S * 18 * W * sizeof(T));
+    uint64_t* empty = full + S;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int rfirst = max(y0 - 2, 0);
+    const int rlast = min(y1 + 1, g.ny - 1);
+    const int x = x0 + t;
+    const bool owner = x < g.nx;
+    const bool dens = x <= g.nx;   // column nx is the periodic ghost of column 0
+    const int e0 = g.origin + x0 - 2;
+    const int slack = e0 % kAlign;
+    const int k = t + 2 + slack;
+    // lanes 0 / 31 also supply the densities of the columns beside the warp
+    const bool halo = lane == 0 || lane == 31;
+    const int kh = lane == 0 ? k - 1 : k + 1;
+    const int sh = lane == 0 ? 0 : 33;
+    const T* win = fin + (e0 - slack);
+    const float shift[2] = {ph.shift[0], ph.shift[1]};
+    const uint32_t row_bytes = W * sizeof(T);
+    float(&ring)[4][2][34] = sR[wid];
+
+    if (t == 0) {
+        for (int j = 0; j < S; ++j) {
+            mbar_init(&full[j], 1);
+            mbar_init(&empty[j], NW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();   // barriers initialised: the only block barrier
+
+    // producer state (warp 0): the next row to issue, its stage, the phase of that
+    // stage's empty barrier to wait for, and whether the stage has been used before
+    int next = rfirst, nj = 0;
+    uint32_t ep = 0;
+    bool reuse = false;
+    auto issue_next = [&]() {   // warp 0, all lanes
+        if (reuse) mbar_wait(&empty[nj], ep, flag);
+        const uint32_t planes = tile_row_planes(next, y0, y1, g.ny);
+        if (lane == 0) mbar_expect_tx(&full[nj], (uint32_t)__popc(planes) * row_bytes);
+        __syncwarp();
+        if (lane < 18 && ((planes >> lane) & 1u)) {
+            fence_proxy_async_smem();
+            bulk_copy_g2s(stage + (size_t)nj * 18 * W + lane * W, win + (size_t)next * g.pitch + (size_t)lane * g.plane,
+                          row_bytes, &full[nj]);
+        }
+        ++next;
+        if (++nj == S) {
+            nj = 0;
+            if (reuse) ep ^= 1u;
+            reuse = true;
+        }
+    };
+    if (wid == 0)
+        while (next <= rlast && next < rfirst + S) issue_next();
+
+    // consumer state (every warp): rows waited for and rows handed back, in order
+    int wr = rfirst, wj = 0;
+    uint32_t wp = 0;
+    auto wait_upto = [&](int r) {
+        for (; wr <= r && wr <= rlast; ++wr) {
+            mbar_wait(&full[wj], wp, flag);
+            if (++wj == S) { wj = 0; wp ^= 1u; }
+        }
+    };
+    int rel = rfirst, rj = 0;
+    auto release_upto = [&](int r) {
+        __syncwarp();
+        for (; rel <= r && rel <= rlast; ++rel) {
+            if (lane == 0) mbar_arrive(&empty[rj]);
+            if (++rj == S) rj = 0;
+        }
+    };
+    // stage of row r (rfirst <= r <= rlast), from the stage jc of a row rc near it
+    auto stage_ptr = [&](int j) -> const T* { return stage + (size_t)j * 18 * W; };
+    auto wrap = [&](int j) { return j < 0 ? j + S : (j >= S ? j - S : j); };
+    // pull of row yo whose own stage is jc (rows yo - 1 / yo + 1 in the stages beside it)
+    auto pull_row = [&](int yo, int jc, int kk, float f[2][9]) {
+        const T* sS = stage_ptr(wrap(jc - 1));
+        const T* sC = stage_ptr(jc);
+        const T* sN = stage_ptr(wrap(jc + 1));
+        if (yo > 0 && yo < g.ny - 1)
+            pull_block<T, TW>(sS, sC, sN, false, false, kk, f);
+        else
+            pull_block<T, TW>(sS, sC, sN, yo == 0, yo == g.ny - 1, kk, f);
+    };
+    auto density = [&](const float* f, int s) {
+        if constexpr (IsShifted<T>::value) return sum9(f) + shift[s];
+        else return sum9(f);
+    };
+    auto densities = [&](int yo, int jc, float f[2][9]) {
+        pull_row(yo, jc, k, f);
+        const int sl = yo & 3;
+        ring[sl][0][lane + 1] = dens ? density(f[0], 0) : 0.0f;
+        ring[sl][1][lane + 1] = dens ? density(f[1], 1) : 0.0f;
+        if (halo) {
+            float fh[2][9];
+            pull_row(yo, jc, kh, fh);
+            ring[sl][0][sh] = density(fh[0], 0);
+            ring[sl][1][sh] = density(fh[1], 1);
+        }
+    };
+    auto zero_row = [&](int yo) {   // the virtual wall rows y = -1 and y = ny
+        const int sl = yo & 3;
+        ring[sl][0][lane + 1] = 0.0f;
+        ring[sl][1][lane + 1] = 0.0f;
+        if (halo) { ring[sl][0][sh] = 0.0f; ring[sl][1][sh] = 0.0f; }
+    };
+
+    // jn: stage of row y + 1 during the collision of row y (rows are consecutive from
+    // rfirst, so the stage of row r is (r - rfirst) mod S)
+    float fa[2][9], fb[2][9];
+    int jy = (y0 - rfirst) % S;   // stage of row y0 (a one-time division)
+    if (y0 > 0) {
+        wait_upto(y0);
+        densities(y0 - 1, wrap(jy - 1), fb);
+    } else {
+        zero_row(y0 - 1);
+    }
+    wait_upto(y0 + 1);
+    densities(y0, jy, fa);
+    release_upto(y0 - 2);
+    if (wid == 0)
+        while (next <= rlast && next - S <= y0 - 2) issue_next();
+    int jn = wrap(jy + 1);
+
+    auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
+        if (y + 1 < g.ny) {
+            wait_upto(y + 2);
+            densities(y + 1, jn, nxt);
+        } else {
+            zero_row(y + 1);
+        }
+        release_upto(y - 1);   // includes the __syncwarp that publishes the ring writes
+        if (wid == 0)
+            while (next <= rlast && next - S <= y - 1) issue_next();
+        jn = wrap(jn + 1);
+        if (owner) {
+            const int s0 = (y - 1) & 3, s1 = y & 3, s2 = (y + 1) & 3;
+            const int c = lane + 1;
+            Nbr pA, pB;
+            pA.E = ring[s1][0][c + 1]; pA.W = ring[s1][0][c - 1];
+            pA.N = ring[s2][0][c];     pA.S = ring[s0][0][c];
+            pA.NE = ring[s2][0][c + 1]; pA.NW = ring[s2][0][c - 1];
+            pA.SE = ring[s0][0][c + 1]; pA.SW = ring[s0][0][c - 1];
+            pB.E = ring[s1][1][c + 1]; pB.W = ring[s1][1][c - 1];
+            pB.N = ring[s2][1][c];     pB.S = ring[s0][1][c];
+            pB.NE = ring[s2][1][c + 1]; pB.NW = ring[s2][1][c - 1];
+            pB.SE = ring[s0][1][c + 1]; pB.SW = ring[s0][1][c - 1];
+            if constexpr (IsShifted<T>::value) {
+                collide_shifted(cur, pA, pB, ph, y, g.ny, flag);
+                store_site_sr<T>(fout, g, y, x, cur, seed);
+            } else {
+                collide_site<true>(cur, pA, pB, ph, y, g.ny, flag);
+                store_site<T>(fout, g, y, x, cur, shift);
+            }
+        }
+    };
+    for (int y = y0; y < y1; y += 2) {
+        row(y, fa, fb);
+        if (y + 1 < y1) row(y + 1, fb, fa);
+    }
+}
+
+template <typename T, int TW>
+__global__ void __launch_bounds__(TW, 512 / TW)
+step_dec_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ DecRingT<TW> sR;
+    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
+    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+    dec_tile<T, TW>(fin, fout, g, ph, blockIdx.x * TW, y0, y1, dsm, sR, seed, flag);
 }
 
 // One grid: block (bx, by) of TW threads takes columns [TW bx, TW bx + TW) and the
@@ -889,6 +1127,8 @@ __device__ __forceinline__ void init_rho(const double* y0, int x, int y, double 
     rB = mB * (eps + (1.0 - eps) * (1.0 - H));
 }
 
+// y0 holds the interface heights of columns -1 .. nx (y0[x + 1]): the population a
+// site sends towards x + c_i is that of the site it reaches, beside the grid too.
 template <typename T>
 __global__ void init_kernel(T* __restrict__ fout, Grid g, float sA, float sB, const double* __restrict__ y0,
                             double mA, double mB, double eps, double width) {
@@ -897,12 +1137,13 @@ __global__ void init_kernel(T* __restrict__ fout, Grid g, float sA, float sB, co
     if (x >= g.nx) return;
     const float shift[2] = {sA, sB};
     double here[2];
+    y0 += 1;
     init_rho(y0, x, y, mA, mB, eps, width, here[0], here[1]);
     float f[2][9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int ty = y + cy(i);
-        const int tx = (x + cx(i) + g.nx) % g.nx;
+        const int tx = x + cx(i);
         double r[2] = {here[0], here[1]};
         if (ty >= 0 && ty < g.ny) init_rho(y0, tx, ty, mA, mB, eps, width, r[0], r[1]);
         for (int s = 0; s < 2; ++s) f[s][i] = (float)(wd(i) * r[s]);
@@ -916,10 +1157,10 @@ __global__ void pull_to_host_kernel(const T* __restrict__ fin, Grid g, float sA,
     const int y = blockIdx.y;
     if (x >= g.nx) return;
     const float shift[2] = {sA, sB};
-    const int xm = x == 0 ? g.nx - 1 : x - 1;
-    const int xp = x == g.nx - 1 ? 0 : x + 1;
+    // the columns beside the grid from the ghost columns (periodic copies, or a split
+    // grid's neighbours)
     float f[2][9];
-    pull_site<T>(fin, g, shift, y, x, xm, xp, f);
+    pull_site<T>(fin, g, shift, y, x, x - 1, x + 1, f);
     const size_t n = (size_t)g.nx * g.ny;
     for (int s = 0; s < 2; ++s)
         for (int i = 0; i < 9; ++i) S[(size_t)(s * 9 + i) * n + (size_t)y * g.nx + x] = (V)f[s][i];
@@ -995,6 +1236,38 @@ static cudaError_t launch_block(const StepLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Resident blocks of step_dec_kernel<T, TW> (attribute set once per instantiation).
+template <typename T, int TW>
+static cudaError_t dec_slots(int* slots) {
+    static int cached = 0;
+    if (cached == 0) {
+        const size_t smem = dec_smem_bytes<T, TW>();
+        cudaError_t e = cudaFuncSetAttribute(step_dec_kernel<T, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_dec_kernel<T, TW>, TW, smem)) != cudaSuccess)
+            return e;
+        cached = std::max(1, sms * occ);
+    }
+    *slots = cached;
+    return cudaSuccess;
+}
+
+template <typename T, int TW>
+static cudaError_t launch_dec(const StepLaunch& L, cudaStream_t st) {
+    const Grid& g = L.grid;
+    int slots = 0;
+    cudaError_t e = dec_slots<T, TW>(&slots);
+    if (e != cudaSuccess) return e;
+    const int gx = (g.nx + TW - 1) / TW;
+    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots));
+    step_dec_kernel<T, TW><<<grid, TW, dec_smem_bytes<T, TW>(), st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, L.flag);
+    return cudaGetLastError();
+}
+
 // Columns per block tile of the block-staged kernel: tile_x when it is 128 or 256;
 // otherwise 256 for 16-bit storage, and for FP32 when the 256-column tiles hold at
 // least kWideMinRows rows (tile_y, or the rows of the one-wave default).  Measured
@@ -1036,6 +1309,11 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         cudaError_t e = block_tile_width<T>(g, L.tile_x, L.tile_y, &tw);
         if (e != cudaSuccess) return e;
         return tw == kWideTileW ? launch_block<T, kWideTileW>(L, st) : launch_block<T, kBlockTileW>(L, st);
+    } else if (kernel == LBM_KERNEL_DECOUPLED) {
+        int tw = 0;
+        cudaError_t e = block_tile_width<T>(g, L.tile_x, L.tile_y, &tw);
+        if (e != cudaSuccess) return e;
+        return tw == kWideTileW ? launch_dec<T, kWideTileW>(L, st) : launch_dec<T, kBlockTileW>(L, st);
     } else if (kernel == LBM_KERNEL_PIPE) {
         const int ty = L.tile_y > 0 ? L.tile_y : 32;
         const size_t smem = pipe_smem_bytes<T>();

@@ -15,7 +15,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3, "pipe": 4}
+KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3, "pipe": 4, "decoupled": 5}
 
 
 class LbmParams(C.Structure):
@@ -29,7 +29,7 @@ class LbmParams(C.Structure):
         ("amp", C.c_double), ("width", C.c_double), ("minority", C.c_double), ("y0", C.c_double),
         ("crop_rows", C.c_int32), ("storage", C.c_int32), ("kernel", C.c_int32), ("tile_y", C.c_int32),
         ("shift_A", C.c_double), ("shift_B", C.c_double),
-        ("tile_x", C.c_int32), ("wall_mode", C.c_int32),
+        ("tile_x", C.c_int32), ("wall_mode", C.c_int32), ("x_offset", C.c_int32), ("nx_total", C.c_int32),
     ]
 
 
@@ -62,6 +62,9 @@ _PROTOS = {
     "lbm_sync": (C.c_int, [_h]),
     "lbm_step_count": (C.c_int, [_h, _P(C.c_int64)]),
     "lbm_step_test_timeout": (C.c_int, [_h]),
+    "lbm_halo_bytes": (C.c_int, [_h, _P(C.c_size_t)]),
+    "lbm_halo_pack": (C.c_int, [_h, C.c_int32, C.c_void_p]),
+    "lbm_halo_unpack": (C.c_int, [_h, C.c_int32, C.c_void_p]),
     "lbm_diagnostics": (C.c_int, [_h, _P(LbmDiag)]),
     "lbm_diagnostics_async": (C.c_int, [_h]),
     "lbm_diagnostics_wait": (C.c_int, [_h, _P(LbmDiag)]),
@@ -237,6 +240,19 @@ class Solver:
 
     def sync(self):
         _check(self.lib.lbm_sync(self._h), "lbm_sync")
+
+    def halo_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(self.lib.lbm_halo_bytes(self._h, C.byref(n)), "lbm_halo_bytes")
+        return n.value
+
+    def halo_pack(self, side: int, dev_ptr: int):
+        """Copy the two edge columns of side 0 (left) or 1 (right) to device memory."""
+        _check(self.lib.lbm_halo_pack(self._h, int(side), C.c_void_p(dev_ptr)), "lbm_halo_pack")
+
+    def halo_unpack(self, side: int, dev_ptr: int):
+        """Copy device memory into the ghost columns of side 0 (left) or 1 (right)."""
+        _check(self.lib.lbm_halo_unpack(self._h, int(side), C.c_void_p(dev_ptr)), "lbm_halo_unpack")
 
     def step_test_timeout(self):
         """One step launch whose row copies are withheld: its bounded waits give up

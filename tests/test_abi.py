@@ -51,8 +51,9 @@ def test_workspace_grows_with_the_grid(lib):
 @pytest.mark.parametrize("field,value", [
     ("nx", 3), ("ny", 7), ("tau_A", 0.5), ("tau_B", 0.4), ("mass_A", 0.0), ("mass_B", -1.0),
     ("width", 0.0), ("minority", 1.0), ("n_modes", 65), ("crop_rows", 2), ("storage", 3),
-    ("kernel", 5), ("tile_y", -1), ("gravity_mode", 2), ("G", float("nan")), ("g", float("inf")),
-    ("tile_x", 64), ("tile_x", -1),
+    ("kernel", 6), ("kernel", -1), ("tile_y", -1), ("gravity_mode", 2), ("G", float("nan")), ("g", float("inf")),
+    ("tile_x", 64), ("tile_x", -1), ("wall_mode", 2), ("wall_mode", -1), ("x_offset", 5), ("x_offset", -1),
+    ("nx_total", -3), ("nx_total", 100),
 ])
 def test_invalid_parameters_are_rejected(lib, field, value):
     p = lbm.default_params()

@@ -13,7 +13,7 @@ from tests import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["fused", "two_pass", "staged", "warp", "pipe"]
+KERNELS = ["fused", "two_pass", "staged", "warp", "pipe", "decoupled"]
 
 
 def oracle_params(d):
@@ -53,13 +53,14 @@ def test_one_step_from_random_populations(gpu, kernel, nx, ny, tile_y):
     assert rel_err(got, ref) < 2e-6
 
 
+@pytest.mark.parametrize("kernel", ["staged", "decoupled"])
 @pytest.mark.parametrize("tile_x", [128, 256])
 @pytest.mark.parametrize("nx,ny,tile_y", CASES)
-def test_block_tile_widths_one_step(gpu, tile_x, nx, ny, tile_y):
-    # the block-staged kernel at each of its tile widths, whatever the default picks
+def test_block_tile_widths_one_step(gpu, kernel, tile_x, nx, ny, tile_y):
+    # the block-staged kernels at each of their tile widths, whatever the default picks
     d = inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=3)
     f = inputs.as_float32(inputs.random_populations(nx * 7 + ny, nx, ny))
-    with lbm.Solver(kernel="staged", tile_x=tile_x, tile_y=tile_y, **d) as s:
+    with lbm.Solver(kernel=kernel, tile_x=tile_x, tile_y=tile_y, **d) as s:
         s.set_populations(f)
         s.step(1)
         got = s.populations()
@@ -80,6 +81,20 @@ def test_tile_widths_give_identical_states(gpu, storage):
             s.step(25)
             states.append(s.populations())
     assert np.array_equal(states[0], states[1]) and np.array_equal(states[1], states[2])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("tile_x,tile_y", [(0, 0), (128, 7), (256, 1)])
+def test_decoupled_kernel_equals_the_staged_one(gpu, storage, tile_x, tile_y):
+    # the same pulls, collision and stores without the block barrier per row: bit for
+    # bit the block-staged kernel's states, ragged tiles and halo rows included
+    d = inputs.params(inputs.C0, nx=600, ny=90, crop_rows=3, g=1e-4, G_wall_A=0.1, wall_mode=1)
+    states = []
+    for kernel in ("staged", "decoupled"):
+        with lbm.Solver(kernel=kernel, storage=storage, tile_x=tile_x, tile_y=tile_y, **d) as s:
+            s.step(25)
+            states.append(s.populations())
+    assert np.array_equal(states[0], states[1])
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -162,7 +177,7 @@ def test_graph_replay_equals_single_launches(gpu):
         assert np.array_equal(a.populations(), b.populations())
 
 
-@pytest.mark.parametrize("other", ["two_pass", "staged", "warp", "pipe"])
+@pytest.mark.parametrize("other", ["two_pass", "staged", "warp", "pipe", "decoupled"])
 def test_kernels_agree(gpu, other):
     # same per-site arithmetic; only the compiler's contraction choices may differ
     d = inputs.params(inputs.C0, nx=200, ny=96)
@@ -172,7 +187,7 @@ def test_kernels_agree(gpu, other):
         assert rel_err(a.populations(), b.populations()) < 1e-6
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged", "warp", "pipe"])
+@pytest.mark.parametrize("kernel", ["fused", "staged", "warp", "pipe", "decoupled"])
 @pytest.mark.parametrize("tile_y", [1, 5, 16, 64, 300])
 def test_tile_shape_does_not_change_the_result(gpu, kernel, tile_y):
     d = inputs.params(inputs.C0, nx=140, ny=150)
@@ -182,7 +197,8 @@ def test_tile_shape_does_not_change_the_result(gpu, kernel, tile_y):
         assert np.array_equal(a.populations(), b.populations())
 
 
-@pytest.mark.parametrize("kernel,tile_x", [("fused", 0), ("staged", 0), ("staged", 256), ("warp", 0), ("pipe", 0)])
+@pytest.mark.parametrize("kernel,tile_x", [("fused", 0), ("staged", 0), ("staged", 256), ("warp", 0), ("pipe", 0),
+                                           ("decoupled", 128), ("decoupled", 256)])
 def test_bench_configuration_one_step_full_grid(gpu, kernel, tile_x):
     # 1024 x 2048 in the launch configurations the benchmark times (default tiles),
     # and the block-staged kernel's wide tile

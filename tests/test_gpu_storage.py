@@ -67,7 +67,7 @@ def test_storage_error_against_the_oracle(gpu, storage, reference):
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("kernel", ["fused", "two_pass", "staged", "warp", "pipe"])
+@pytest.mark.parametrize("kernel", ["fused", "two_pass", "staged", "warp", "pipe", "decoupled"])
 def test_one_step_of_the_16bit_storage(gpu, storage, kernel):
     # the state the storage holds (rounded) is read back and stepped by the oracle
     nx, ny = 150, 40
