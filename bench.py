@@ -277,11 +277,53 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks.summary(),
     }
+    if ws == 1 and not args.no_extra_lines and (args.nx, args.ny) == (1024, 2048):
+        # the full-size grid (10000 x 5000) in FP32 and in FP16 storage, same kernels and
+        # timing (100 LB steps + diagnostics per bench step): the size at which storage
+        # types are compared
+        out["full_size"] = {st: grid_line(args, 10000, 5000, st) for st in ("f32", "f16")}
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def grid_line(args, nx, ny, storage, steps=3, warmup=3):
+    """MLUPS and HBM-roofline fraction of the step kernel on an nx x ny grid with the
+    bench step of run_ours (100 LB steps + one diagnostics evaluation), CUDA events on
+    the solver's stream."""
+    import torch
+
+    from paper_2101_04847_gb300 import lbm
+
+    params = workload(args)
+    params.update(nx=nx, ny=ny, seed=1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = lbm.Solver(storage=storage, kernel=args.kernel, tile_y=args.tile_y, **params)
+    for _ in range(warmup):
+        s.step(LB_STEPS_PER_STEP)
+        s.diagnostics()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        s.step(LB_STEPS_PER_STEP)
+        b.record(stream)
+        s.diagnostics()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    total_ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in ev) / (steps * LB_STEPS_PER_STEP)
+    peak, _ = measured_peak_hbm()
+    frac = BYTES_PER_SITE[storage] * nx * ny / (kernel_ms * 1e-3) / 1e9 / peak
+    return {"value": round(nx * ny * LB_STEPS_PER_STEP * steps / (total_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "roofline_frac": round(frac, 4), "launch_ms": round(kernel_ms, 5),
+            "bytes_per_site": BYTES_PER_SITE[storage], "steps": steps, "warmup": warmup}
 
 
 def _splitmix64(state: int):
@@ -440,14 +482,16 @@ def run_storage_study(args):
 
 
 # The paper's production case (Section 2, parameter paragraph): tau = 0.53 (nu = 0.01),
-# pure densities 1.10, g = 9e-6, 10000 x 5000, 90 000 steps; G_AB = 0.1381 (immiscible,
-# each phase holding the coexistence fraction 6.8 % of the other component) or 0.0805
-# (miscible, pure phases).  The white-noise interface deformation of amplitude 4 is
+# pure densities 1.10, g = 9e-6, 10000 x 5000, 90 000 steps; G_AB = 0.1381 (immiscible)
+# or 0.0805 (miscible).  Both start, as the paper's runs do, from the immiscible model's
+# equilibrium configuration: each phase holds the coexistence fraction 6.8 % of the
+# other component (pure phases would put the absent component 0.3 % below zero within
+# a few steps of the over-relaxed BGK update at tau = 0.53).  The white-noise interface deformation of amplitude 4 is
 # read as seeded sinusoidal modes normalised to amplitude 4, one mode per 128 columns
 # up to 64 (at 10000 columns: wavelengths of 156 cells and more; shorter waves than
 # the interface is wide drive the densities negative in the first steps).
 PAPER_CASE = dict(tau_A=0.53, tau_B=0.53, mass_A=1.1, mass_B=1.1, g=9e-6, amp=4.0, width=1.5, crop_rows=10)
-PAPER_COUPLING = {"immiscible": dict(G=0.1381, minority=0.068), "miscible": dict(G=0.0805, minority=0.0)}
+PAPER_COUPLING = {"immiscible": dict(G=0.1381, minority=0.068), "miscible": dict(G=0.0805, minority=0.068)}
 # surface tension of the immiscible model under this reading: the flat interface's stress
 # excess in the FP64 oracle (0.0046; the Laplace law of droplets gives the same); the
 # paper quotes 0.0059
@@ -499,6 +543,8 @@ def run_paper_case(args):
         rates[case] = {"MLUPS": round(args.nx * args.ny * len(seeds) * every * nchk / (ms * 1e-3) / 1e6, 1),
                        "seconds": round(ms / 1e3, 1), "clocks": clocks.summary(), "status": status}
         results[case] = series
+        if args.paper_out:   # the raw series so far, in case a later case does not finish
+            Path(args.paper_out + ".partial").write_text(json.dumps({"rates": rates, "series": results}))
     steps = [every * i for i in range(nchk + 1)]
     sub = args.nx * (args.ny - 2 * PAPER_CASE["crop_rows"])
     out = {"kind": "paper_case", "grid": f"{args.nx}x{args.ny}", "steps": total, "every": every,
@@ -544,8 +590,9 @@ def run_paper_case(args):
     if args.paper_out:
         Path(args.paper_out).write_text(json.dumps(out))
     summary = {k: v for k, v in out.items() if k not in ("cases",) and not k.endswith("_f16_vs_f32")}
-    summary["final"] = {case: {k: [round(out["cases"][case]["series"][k]["mean"][-1], 8),
-                                   round(out["cases"][case]["series"][k]["std"][-1], 8)]
+    sig = lambda v: float(f"{v:.6g}")
+    summary["final"] = {case: {k: [sig(out["cases"][case]["series"][k]["mean"][-1]),
+                                   sig(out["cases"][case]["series"][k]["std"][-1])]
                                for k in ("h", "E_k", "E_p", "L_int")} for case in out["cases"]}
     for case in out["cases"]:
         if "interface_energy" in out["cases"][case]:
@@ -817,6 +864,8 @@ def main():
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-lines", dest="no_extra_lines", action="store_true",
+                    help="skip the 10000x5000 FP32 / FP16 lines added to the default run")
     ap.add_argument("--ensemble", type=int, default=0, help="run the batched-ensemble workload with this many members")
     ap.add_argument("--ensemble-grid", dest="ensemble_grid", default="",
                     help="with --ensemble: put every member on this NXxNY grid instead of the drawn ones")
