@@ -50,10 +50,10 @@ typedef enum {
     LBM_EINVAL = 1,     /* invalid argument or parameter set */
     LBM_ENOMEM = 2,     /* allocation failed or workspace too small */
     LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
-    LBM_EUNSTABLE = 4,  /* sticky: a NaN or a negative density was seen by the step: below
-                         * -0.1 % (FP32), -1 % (FP16) or -5 % (BF16) of rho0_s =
-                         * mass_s (1 + minority) / 2, which leaves room for the rounding-level
-                         * values of an absent component */
+    LBM_EUNSTABLE = 4,  /* sticky: a non-finite density, or one below -5 % of rho0_s =
+                         * mass_s (1 + minority) / 2, was seen by the step (small transient
+                         * negative values of a nearly absent component are part of the
+                         * over-relaxed update near tau = 1/2, not a blow-up) */
     LBM_ETIMEOUT = 5,   /* sticky: a bounded device-side wait gave up */
     LBM_ESTATE = 6,     /* call not valid in the handle's current state */
     LBM_EIO = 7         /* file I/O error (save/load) */
@@ -72,8 +72,11 @@ typedef enum {
                               * block-wide sweep (the default: the fastest; the ensemble's tile code) */
     LBM_KERNEL_WARP = 3,     /* as STAGED, one independent sweep per warp */
     LBM_KERNEL_PIPE = 4,     /* as STAGED, warps sweep independently over shared stages (no block barrier) */
-    LBM_KERNEL_DECOUPLED = 5 /* as STAGED (same tiles and row stages), but no block barrier per row: each warp
+    LBM_KERNEL_DECOUPLED = 5,/* as STAGED (same tiles and row stages), but no block barrier per row: each warp
                               * keeps its own density ring, stages are handed back through per-stage barriers */
+    LBM_KERNEL_PAIRED = 6    /* 16-bit storage only: as STAGED with 256-column tiles, each thread owning two
+                              * neighbouring columns (per-row work shared by two sites, paired 32-bit stores);
+                              * what STAGED runs for 16-bit storage when tile_x is 0 */
 } lbm_kernel;
 
 /* Parameters (lattice units, dx = dt = 1).  lbm_params_default() fills them. */
@@ -100,10 +103,12 @@ typedef struct {
                               * rows are split evenly over the tiles); 0 = the kernel's default
                               * (block-staged: one wave of tiles filling every SM) */
     double shift_A, shift_B; /* rho0_s of the shifted storage; <= 0 means (mass_s (1 + minority)) / 2 */
-    int32_t tile_x;          /* columns per block tile of the block-staged kernel: 128 or 256;
-                              * 0 = chosen per grid (256 for 16-bit storage, and for FP32 when
-                              * the 256-column tiles are at least 64 rows tall).  Other kernels
-                              * and ensembles (128 columns) ignore it. */
+    int32_t tile_x;          /* columns per block tile of the block-staged kernel: 128 or 256
+                              * (one column per thread); 0 = chosen per grid: for 16-bit storage
+                              * the paired-column tile (256 columns, two per thread, the
+                              * LBM_KERNEL_PAIRED kernel), for FP32 256 when the 256-column tiles
+                              * are at least 64 rows tall, else 128.  Other kernels ignore it;
+                              * ensembles take 128 or 256 (lbm_ens_tune). */
     int32_t wall_mode;       /* pseudopotential beyond the walls in the Shan-Chen force (Section 2
                               * leaves it open): 0 = none (psi = 0 on the virtual rows y = -1 and
                               * y = ny); 1 = mirror (those rows hold the wall rows' own psi: a
@@ -265,7 +270,8 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 void lbm_destroy(lbm_handle* h);
 
 /* Pick the rows per tile (tile_y) of the handle's step kernel, and for the
- * block-staged kernel the columns per tile (tile_x, 128 or 256), by timing candidate
+ * block-staged kernel the columns per tile (tile_x: 128 or 256, and for 16-bit
+ * storage also 0, the paired-column tile), by timing candidate
  * values (0 = the default among them) on the handle's own grid, then use the
  * fastest; lbm_get_params reports both.  The state and the step counter are left as
  * they were.  cache_path: NULL, or a text file of
@@ -301,9 +307,14 @@ lbm_status lbm_ens_member(lbm_ensemble* e, int32_t i, lbm_handle** out);
 /* Diagnostics of every member into out[0..n-1]; synchronises. */
 lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out);
 
-/* Pick tile_y for the whole ensemble by timing candidates (0, the slot-filling
- * default, among them); states are kept.  tile_y receives the rows per tile in use. */
+/* Pick the tile shape for the whole ensemble by timing candidates: tile widths of 128
+ * and 256 columns (threads per block) times tile heights (0, the slot-filling
+ * default, among them); states are kept.  tile_y receives the rows per tile in use.
+ * The initial width is the first member's tile_x when it is 256, else 128. */
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y, double* ms_per_step);
+
+/* Columns per tile of the ensemble's launch (128 or 256). */
+lbm_status lbm_ens_tile_width(lbm_ensemble* e, int32_t* tile_x);
 
 void lbm_ens_destroy(lbm_ensemble* e);
 

@@ -33,6 +33,7 @@ struct lbm_ensemble {
     std::vector<lbm::EnsMember> table;
     lbm::EnsMember* d_table = nullptr;
     int total_tiles = 0;
+    int tile_x = lbm::kBlockTileW;   // columns per tile (and threads per block): 128 or 256
     int tile_y = 0;       // requested rows per tile; 0: chosen from the device's block slots
     int rows = 0;         // rows per tile in use
     size_t smem = 0;      // dynamic shared memory per block (largest storage type present)
@@ -52,8 +53,8 @@ void ens_drop_graphs(lbm_ensemble* e) {
     }
 }
 
-int tiles_of(const lbm::Grid& g, int rows, int* tx, int* ty) {
-    *tx = (g.nx + lbm::kBlockTileW - 1) / lbm::kBlockTileW;
+int tiles_of(const lbm::Grid& g, int tile_x, int rows, int* tx, int* ty) {
+    *tx = (g.nx + tile_x - 1) / tile_x;
     *ty = std::min(g.ny, std::max(1, (g.ny + rows - 1) / rows));
     return *tx * *ty;
 }
@@ -68,7 +69,7 @@ int auto_rows(const lbm_ensemble* e, int slots) {
         long long tiles = 0;
         for (lbm_handle* h : e->members) {
             int tx, ty;
-            tiles += tiles_of(lbm::handle_grid(h), rows, &tx, &ty);
+            tiles += tiles_of(lbm::handle_grid(h), e->tile_x, rows, &tx, &ty);
         }
         const long long waves = (tiles + slots - 1) / slots;
         const double score = (double)tiles / (double)(waves * slots) * rows / (rows + 3.0);
@@ -85,12 +86,12 @@ lbm_status ens_build_table(lbm_ensemble* e) {
     e->table.clear();
     e->smem = 0;
     for (lbm_handle* h : e->members)
-        e->smem = std::max(e->smem, lbm::block_tile_smem_bytes(lbm::handle_params(h).storage));
+        e->smem = std::max(e->smem, lbm::block_tile_smem_bytes(lbm::handle_params(h).storage, e->tile_x));
     if (e->tile_y > 0) {
         e->rows = e->tile_y;
     } else {
         cudaError_t err = cudaSuccess;
-        const int slots = lbm::ensemble_slots(e->smem, &err);
+        const int slots = lbm::ensemble_slots(e->smem, e->tile_x, &err);
         ENS_TRY(err, "ensemble occupancy");
         e->rows = auto_rows(e, slots);
     }
@@ -111,7 +112,7 @@ lbm_status ens_build_table(lbm_ensemble* e) {
         m.flag = lbm::handle_flag(h);
         m.storage = lbm::handle_params(h).storage;
         m.step_ctr = lbm::handle_step_counters(h);
-        const int tiles = tiles_of(m.grid, e->rows, &m.tiles_x, &m.tiles_y);
+        const int tiles = tiles_of(m.grid, e->tile_x, e->rows, &m.tiles_x, &m.tiles_y);
         m.tile_begin = begin;
         begin += tiles;
         e->table.push_back(m);
@@ -127,7 +128,7 @@ lbm_status ens_build_table(lbm_ensemble* e) {
 lbm_status ens_launch(lbm_ensemble* e, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
         ENS_TRY(lbm::launch_ensemble_step(e->d_table, (int)e->members.size(), e->total_tiles, e->parity, e->smem,
-                                          e->stream),
+                                          e->tile_x, e->stream),
                 "ensemble step");
         e->parity ^= 1;
     }
@@ -141,7 +142,7 @@ lbm_status ens_graph(lbm_ensemble* e, cudaGraphExec_t* out) {
         ENS_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         for (int k = 0; k < kEnsGraphChunk; ++k) {
             cudaError_t err = lbm::launch_ensemble_step(e->d_table, (int)e->members.size(), e->total_tiles,
-                                                        (par + k) & 1, e->smem, e->stream);
+                                                        (par + k) & 1, e->smem, e->tile_x, e->stream);
             if (err != cudaSuccess) {
                 cudaStreamEndCapture(e->stream, &g);
                 if (g) cudaGraphDestroy(g);
@@ -190,6 +191,7 @@ lbm_status lbm_ens_create(int32_t n, const lbm_params* params, void* cuda_stream
         e->own_stream = true;
     }
     e->tile_y = params[0].tile_y > 0 ? params[0].tile_y : 0;
+    e->tile_x = params[0].tile_x == lbm::kWideTileW ? lbm::kWideTileW : lbm::kBlockTileW;
     for (int i = 0; i < n; ++i) {
         lbm_params p = params[i];
         p.kernel = LBM_KERNEL_STAGED;
@@ -268,14 +270,17 @@ lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out) {
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y_out, double* ms_out) {
     if (!e) return ens_fail(LBM_EINVAL, "ensemble is NULL");
     const int cand[] = {0, 12, 16, 20, 24, 32, 48, 64, 96};   // 0: the slot-filling default
+    const int widths[] = {lbm::kBlockTileW, lbm::kWideTileW};
     cudaEvent_t a, b;
     ENS_TRY(cudaEventCreate(&a), "event");
     ENS_TRY(cudaEventCreate(&b), "event");
     for (lbm_handle* h : e->members) ENS_TRY(lbm::handle_save_state(h), "save state");
     const int par0 = e->parity;
     double best_ms = 1e30;
-    int best_ty = e->tile_y;
+    int best_ty = e->tile_y, best_tx = e->tile_x;
+    for (int tx : widths)
     for (int ty : cand) {
+        e->tile_x = tx;
         e->tile_y = ty;
         lbm_status st = ens_build_table(e);
         const int reps = 6;
@@ -298,15 +303,23 @@ lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y_out, double* ms_out) {
         if (ms / reps < best_ms) {
             best_ms = ms / reps;
             best_ty = ty;
+            best_tx = tx;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    e->tile_x = best_tx;
     e->tile_y = best_ty;
     lbm_status st = ens_build_table(e);
     if (st != LBM_OK) return st;
     if (tile_y_out) *tile_y_out = e->rows;
     if (ms_out) *ms_out = best_ms;
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_tile_width(lbm_ensemble* e, int32_t* tile_x) {
+    if (!e || !tile_x) return ens_fail(LBM_EINVAL, "NULL argument");
+    *tile_x = e->tile_x;
     return LBM_OK;
 }
 

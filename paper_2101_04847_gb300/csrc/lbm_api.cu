@@ -129,7 +129,9 @@ lbm_status validate(const lbm_params* p) {
     if (p->n_modes < 0 || p->n_modes > 64) return fail(LBM_EINVAL, "n_modes must be in [0, 64]");
     if (p->crop_rows < 3 || 2 * p->crop_rows >= p->ny) return fail(LBM_EINVAL, "crop_rows must be >= 3 and 2*crop_rows < ny");
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16) return fail(LBM_EINVAL, "unknown storage");
-    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_DECOUPLED) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel < LBM_KERNEL_FUSED || p->kernel > LBM_KERNEL_PAIRED) return fail(LBM_EINVAL, "unknown kernel");
+    if (p->kernel == LBM_KERNEL_PAIRED && p->storage == LBM_STORE_F32)
+        return fail(LBM_EINVAL, "the paired-column kernel is for 16-bit storage");
     if (p->tile_y < 0 || p->tile_y > 4096) return fail(LBM_EINVAL, "tile_y must be in [0, 4096]");
     if (p->tile_x != 0 && p->tile_x != 128 && p->tile_x != 256) return fail(LBM_EINVAL, "tile_x must be 0, 128 or 256");
     if (p->gravity_mode < 0 || p->gravity_mode > 1) return fail(LBM_EINVAL, "gravity_mode must be 0 or 1");
@@ -424,11 +426,13 @@ extern "C" lbm_status lbm_tune(lbm_handle* h, const char* cache_path, int32_t* t
         destroy_graphs(h);
     } else {
         const int cand[] = {0, 8, 12, 16, 24, 32, 48, 64, 96, 128};   // 0: the kernel's own default
-        // tile widths: the block-staged kernel has two; the others ignore tile_x
-        const int xs_staged[] = {lbm::kBlockTileW, lbm::kWideTileW}, xs_other[] = {0};
+        // tile widths: the block-staged kernel has two, and for 16-bit storage also
+        // the paired-column tile (tile_x 0); the others ignore tile_x
+        const int xs_staged[] = {lbm::kBlockTileW, lbm::kWideTileW, 0}, xs_other[] = {0};
         const bool staged = h->p.kernel == LBM_KERNEL_STAGED || h->p.kernel == LBM_KERNEL_DECOUPLED;
+        const bool paired_too = h->p.kernel == LBM_KERNEL_STAGED && h->p.storage != LBM_STORE_F32;
         const int* xs = staged ? xs_staged : xs_other;
-        const int nxs = staged ? 2 : 1;
+        const int nxs = staged ? (paired_too ? 3 : 2) : 1;
         cudaEvent_t a, b;
         LBM_TRY(cudaEventCreate(&a), "event");
         LBM_TRY(cudaEventCreate(&b), "event");
@@ -612,16 +616,15 @@ lbm_status lbm_create_ex(const lbm_params* p, void* dev_workspace, size_t ws_byt
     ph.wall_mirror = p->wall_mode == 1 ? 1 : 0;
     ph.shift[0] = h->shift[0];
     ph.shift[1] = h->shift[1];
-    // The instability guard rejects negative densities.  A component absent from a
-    // phase (minority 0) has density 0 there, and near a front the over-relaxation of
-    // tau < 1 sends it a few rounding units below zero (1e-17 at tau = 0.53 in FP32).
-    // 16-bit storage cannot hold a pure phase exactly (h = -w rho0 is not on its
-    // grid), and its stochastic rounding makes the density of an absent component
-    // fluctuate around zero by a few units of the stored spacing.  So the guard
-    // accepts down to -0.1 % (FP32), -1 % (FP16) or -5 % (BF16) of
-    // rho0_s = mass_s (1 + minority) / 2, far above the rounding noise and far below
-    // a real blow-up.
-    const float floor_frac = p->storage == LBM_STORE_F16 ? 0.01f : (p->storage == LBM_STORE_BF16 ? 0.05f : 0.001f);
+    // The instability guard rejects densities below -5 % of rho0_s = mass_s (1 + minority)
+    // / 2, and non-finite ones.  Zero is not the floor: near tau = 1/2 the over-relaxed
+    // BGK update sends the density of a component that is nearly absent at a site below
+    // zero for a while (the minority component in the thin filaments of the paper's
+    // turbulent mixing layer at tau = 0.53, measured on the 10000 x 5000 grid after
+    // ~29 000 steps; an absent component a few rounding units below zero near a front;
+    // the 16-bit storage's rounding noise around zero), without any blow-up, which
+    // grows past any such floor within a few steps or turns a density non-finite.
+    const float floor_frac = 0.05f;
     ph.rho_floor[0] = (float)(-floor_frac * sA);
     ph.rho_floor[1] = (float)(-floor_frac * sB);
     ph.step_in = nullptr;    // set per launch (step_launch)

@@ -100,11 +100,11 @@ struct EnsMember {
 int warp_tiles(const Grid& g, int tile_y, int* tiles_x);
 int default_tile_y();
 // dynamic shared memory of one block tile for a storage type
-size_t block_tile_smem_bytes(int storage);
+size_t block_tile_smem_bytes(int storage, int tile_x);
 // resident blocks of the ensemble kernel on the current device with `smem` bytes each
-int ensemble_slots(size_t smem, cudaError_t* err);
+int ensemble_slots(size_t smem, int tile_x, cudaError_t* err);
 cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, size_t smem,
-                                 cudaStream_t st);
+                                 int tile_x, cudaStream_t st);
 
 // handle accessors for the ensemble (lbm_api.cu)
 void* handle_buffer(lbm_handle* h, int k);

@@ -959,6 +959,237 @@ step_dec_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics
     dec_tile<T, TW>(fin, fout, g, ph, blockIdx.x * TW, y0, y1, dsm, sR, seed, flag);
 }
 
+// ---------------------------------------------------------------------------
+// Paired-column block tile for 16-bit storage.  The rows, stages and pulls of
+// block_tile with tiles of kWideTileW columns, but half as many threads: thread t
+// owns the neighbouring columns x0 + 2t and x0 + 2t + 1.  The per-row work that does
+// not depend on the site (the waits, stage addressing, the block barrier, the copy
+// issue, loop control) is then shared by two sites, and a column pair's stores are
+// one 32-bit store per plane.  Registers stay low because a site's populations are
+// pulled again after the barrier (the densities pass before it keeps only sums), so
+// a stage is refilled only once the row two below the current one is done with: one
+// row less of prefetch than block_tile.
+// The arithmetic, and the stochastic rounding's random bits, are those of
+// block_tile: the results are identical bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int kPairThreads = kWideTileW / 2;
+template <typename T> using PairRingT = float[4][2][kWideTileW + 2];
+
+template <typename T>
+__host__ __device__ constexpr size_t pair_smem_bytes() {
+    return (size_t)kBlockStages * 18 * BlockWin<T, kWideTileW>::value * sizeof(T) + kBlockStages * sizeof(uint64_t);
+}
+
+// The 18 values of site (x, y) with store_site_sr's random bits added below the
+// 16-bit mantissa: rounding them toward zero gives store_site_sr's stochastic rounding.
+template <typename T> struct SrBits;
+template <> struct SrBits<__half> { static constexpr int kDrop = 13; };
+template <> struct SrBits<__nv_bfloat16> { static constexpr int kDrop = 16; };
+
+template <typename T>
+__device__ __forceinline__ void dither_site(const Grid& g, int y, int x, const float h[2][9], uint32_t seed,
+                                            float d[2][9]) {
+    const uint32_t site = g.nx_total > 0 ? (uint32_t)y * (uint32_t)g.nx_total + (uint32_t)(g.x_offset + x)
+                                         : (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        uint32_t r = hash_lowbias32((site * 2u + (uint32_t)s) ^ seed);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            r = r * 747796405u + 2891336453u;
+            d[s][i] = __uint_as_float(__float_as_uint(h[s][i]) + (r >> (32 - SrBits<T>::kDrop)));
+        }
+    }
+}
+
+// Two values rounded toward zero and packed: lo in bits 0-15, hi in bits 16-31.
+template <typename T> __device__ __forceinline__ uint32_t pack_rz(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack_rz<__half>(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+template <> __device__ __forceinline__ uint32_t pack_rz<__nv_bfloat16>(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+template <typename T> __device__ __forceinline__ T to_rz(float v);
+template <> __device__ __forceinline__ __half to_rz<__half>(float v) { return __float2half_rz(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_rz<__nv_bfloat16>(float v) { return __float2bfloat16_rz(v); }
+
+template <typename T>
+__device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restrict__ fout, const Grid& g,
+                                          const Physics& ph, int x0, int y0, int y1, unsigned char* dsm,
+                                          PairRingT<T>& sR, uint32_t seed, int* flag) {
+    constexpr int TW = kWideTileW;
+    constexpr int W = BlockWin<T, TW>::value;
+    constexpr int kAlign = BlockWin<T, TW>::kAlign;
+    T* stage = reinterpret_cast<T*>(dsm);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kBlockStages * 18 * W * sizeof(T));
+    const int t = threadIdx.x;
+    const int rfirst = max(y0 - 2, 0);
+    const int rlast = min(y1 + 1, g.ny - 1);
+    const int xa = x0 + 2 * t;
+    const bool own_a = xa < g.nx, own_b = xa + 1 < g.nx;
+    const bool dens_a = xa <= g.nx, dens_b = xa + 1 <= g.nx;   // column nx: ghost of column 0
+    const int e0 = g.origin + x0 - 2;
+    const int slack = e0 % kAlign;
+    const int ka = 2 * t + 2 + slack;   // window column of xa
+    // threads 64 / 65: the halo columns x0 - 1 / x0 + TW
+    const bool halo = t == 64 || t == 65;
+    const int kh = t == 64 ? 1 + slack : TW + 2 + slack;
+    const int sh = t == 64 ? 0 : TW + 1;
+    const T* win = fin + (e0 - slack);
+    const uint32_t row_bytes = W * sizeof(T);
+
+    if (t == 0) {
+        for (int j = 0; j < kBlockStages; ++j) mbar_init(&bar[j], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int next = rfirst;
+    auto issue = [&](int r) {   // warp 0, all lanes
+        const int j = (r - rfirst) % kBlockStages;
+        uint64_t* b = &bar[j];
+        const uint32_t planes = tile_row_planes(r, y0, y1, g.ny);
+        if (t == 0) mbar_expect_tx(b, (uint32_t)__popc(planes) * row_bytes);
+        __syncwarp();
+        if (t < 18 && ((planes >> t) & 1u))
+            bulk_copy_g2s(stage + (size_t)j * 18 * W + t * W, win + (size_t)r * g.pitch + (size_t)t * g.plane,
+                          row_bytes, b);
+    };
+    if (t < 32)
+        for (; next <= rlast && next < rfirst + kBlockStages; ++next) issue(next);
+    auto wait_row = [&](int r) {
+        if (r >= rfirst && r <= rlast)
+            mbar_wait(&bar[(r - rfirst) % kBlockStages], (uint32_t)(((r - rfirst) / kBlockStages) & 1), flag);
+    };
+    auto stage_of = [&](int r) -> const T* {
+        const int rr = min(max(r, rfirst), rlast);
+        return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * W;
+    };
+    auto pull_row = [&](int yo, const T* sS, const T* sC, const T* sN, int kk, float f[2][9]) {
+        if (yo > 0 && yo < g.ny - 1)
+            pull_block<T, TW>(sS, sC, sN, false, false, kk, f);
+        else
+            pull_block<T, TW>(sS, sC, sN, yo == 0, yo == g.ny - 1, kk, f);
+    };
+    // densities of row yo into ring slot yo & 3 (16-bit storage holds h = f - w rho0)
+    auto densities = [&](int yo) {
+        const T *sS = stage_of(yo - 1), *sC = stage_of(yo), *sN = stage_of(yo + 1);
+        const int sl = yo & 3;
+        float f[2][9];
+        pull_row(yo, sS, sC, sN, ka, f);
+        sR[sl][0][2 * t + 1] = dens_a ? sum9(f[0]) + ph.shift[0] : 0.0f;
+        sR[sl][1][2 * t + 1] = dens_a ? sum9(f[1]) + ph.shift[1] : 0.0f;
+        pull_row(yo, sS, sC, sN, ka + 1, f);
+        sR[sl][0][2 * t + 2] = dens_b ? sum9(f[0]) + ph.shift[0] : 0.0f;
+        sR[sl][1][2 * t + 2] = dens_b ? sum9(f[1]) + ph.shift[1] : 0.0f;
+        if (halo) {
+            pull_row(yo, sS, sC, sN, kh, f);
+            sR[sl][0][sh] = sum9(f[0]) + ph.shift[0];
+            sR[sl][1][sh] = sum9(f[1]) + ph.shift[1];
+        }
+    };
+    auto zero_row = [&](int yo) {
+        const int sl = yo & 3;
+        sR[sl][0][2 * t + 1] = 0.0f; sR[sl][1][2 * t + 1] = 0.0f;
+        sR[sl][0][2 * t + 2] = 0.0f; sR[sl][1][2 * t + 2] = 0.0f;
+        if (halo) { sR[sl][0][sh] = 0.0f; sR[sl][1][sh] = 0.0f; }
+    };
+    // collide the site in ring column c (window column kk) of row y; out: its values
+    // with the stochastic rounding's bits added, to be rounded toward zero
+    auto site = [&](int y, const T* sS, const T* sC, const T* sN, int kk, int c, int x, float out[2][9]) {
+        float h[2][9];
+        pull_row(y, sS, sC, sN, kk, h);
+        const int s0 = (y - 1) & 3, s1 = y & 3, s2 = (y + 1) & 3;
+        Nbr pA, pB;
+        pA.E = sR[s1][0][c + 1]; pA.W = sR[s1][0][c - 1];
+        pA.N = sR[s2][0][c];     pA.S = sR[s0][0][c];
+        pA.NE = sR[s2][0][c + 1]; pA.NW = sR[s2][0][c - 1];
+        pA.SE = sR[s0][0][c + 1]; pA.SW = sR[s0][0][c - 1];
+        pB.E = sR[s1][1][c + 1]; pB.W = sR[s1][1][c - 1];
+        pB.N = sR[s2][1][c];     pB.S = sR[s0][1][c];
+        pB.NE = sR[s2][1][c + 1]; pB.NW = sR[s2][1][c - 1];
+        pB.SE = sR[s0][1][c + 1]; pB.SW = sR[s0][1][c - 1];
+        collide_shifted(h, pA, pB, ph, y, g.ny, flag);
+        dither_site<T>(g, y, x, h, seed, out);
+    };
+    auto ghost = [&](int y, int x, const float v[2][9]) {   // periodic copies of the two first / last columns
+        if (x < 2 || x >= g.nx - 2) {
+            T* qg = fout + (size_t)y * g.pitch + g.origin + x + (x < 2 ? g.nx : -g.nx);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) qg[(size_t)(s * 9 + i) * g.plane] = to_rz<T>(v[s][i]);
+        }
+    };
+
+    if (y0 > 0) {
+        wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
+        densities(y0 - 1);
+    } else {
+        zero_row(y0 - 1);
+    }
+    wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
+    densities(y0);
+    __syncthreads();
+    if (t < 32) {
+        fence_proxy_async_smem();
+        for (; next <= rlast && next - kBlockStages <= y0 - 2; ++next) issue(next);
+    }
+    for (int y = y0; y < y1; ++y) {
+        if (y + 1 < g.ny) {
+            wait_row(y + 2);
+            densities(y + 1);
+        } else {
+            zero_row(y + 1);
+        }
+        __syncthreads();
+        // every thread is past its reads of rows < y - 1 (the sites below pull row
+        // y - 1 again after the barrier): refill those stages
+        if (t < 32) {
+            fence_proxy_async_smem();
+            for (; next <= rlast && next - kBlockStages <= y - 2; ++next) issue(next);
+        }
+        if (own_a) {
+            const T *sS = stage_of(y - 1), *sC = stage_of(y), *sN = stage_of(y + 1);
+            float va[2][9], vb[2][9];
+            site(y, sS, sC, sN, ka, 2 * t + 1, xa, va);
+            T* q = fout + (size_t)y * g.pitch + g.origin + xa;
+            if (own_b) {
+                site(y, sS, sC, sN, ka + 1, 2 * t + 2, xa + 1, vb);
+                // one conversion and one 32-bit store per plane for the column pair
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        *reinterpret_cast<uint32_t*>(q + (size_t)(s * 9 + i) * g.plane) = pack_rz<T>(va[s][i], vb[s][i]);
+                ghost(y, xa + 1, vb);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) q[(size_t)(s * 9 + i) * g.plane] = to_rz<T>(va[s][i]);
+            }
+            ghost(y, xa, va);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPairThreads, 4)
+step_pair_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ PairRingT<T> sR;
+    const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
+    const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
+    const uint32_t seed = launch_seed(ph);
+    advance_step(ph, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+    pair_tile<T>(fin, fout, g, ph, blockIdx.x * kWideTileW, y0, y1, dsm, sR, seed, flag);
+}
+
 // One grid: block (bx, by) of TW threads takes columns [TW bx, TW bx + TW) and the
 // by-th of gridDim.y tiles of (nearly) equal height.
 template <typename T, int TW>
@@ -992,10 +1223,11 @@ step_block_timeout_kernel(const float* __restrict__ fin, float* __restrict__ fou
 // the member's grid, physics and storage type; no member waits for another, so
 // uneven grids need no barrier.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlockTileW, 512 / kBlockTileW)
+template <int TW>
+__global__ void __launch_bounds__(TW, 512 / TW)
 ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ BlockRing sR;
+    __shared__ BlockRingT<TW> sR;
     const int tile = blockIdx.x;
     int lo = 0, hi = n - 1;   // last member whose first tile is <= tile
     while (lo < hi) {
@@ -1017,47 +1249,64 @@ ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     advance_step(ph, local == 0 && threadIdx.x == 0);
     switch (M.storage) {
         case LBM_STORE_F16:
-            block_tile<__half>((const __half*)fin, (__half*)fout, M.grid, ph, tx * kBlockTileW, y0, y1, dsm, sR,
-                               seed, M.flag);
+            block_tile<__half, TW>((const __half*)fin, (__half*)fout, M.grid, ph, tx * TW, y0, y1, dsm, sR, seed,
+                                   M.flag);
             break;
         case LBM_STORE_BF16:
-            block_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph,
-                                      tx * kBlockTileW, y0, y1, dsm, sR, seed, M.flag);
+            block_tile<__nv_bfloat16, TW>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph, tx * TW, y0,
+                                          y1, dsm, sR, seed, M.flag);
             break;
         default:
-            block_tile<float>((const float*)fin, (float*)fout, M.grid, ph, tx * kBlockTileW, y0, y1, dsm, sR,
-                              seed, M.flag);
+            block_tile<float, TW>((const float*)fin, (float*)fout, M.grid, ph, tx * TW, y0, y1, dsm, sR, seed,
+                                  M.flag);
     }
 }
 
-size_t block_tile_smem_bytes(int storage) {
+size_t block_tile_smem_bytes(int storage, int tile_x) {
+    if (tile_x == kWideTileW)
+        return storage == LBM_STORE_F32 ? block_smem_bytes<float, kWideTileW>() : block_smem_bytes<__half, kWideTileW>();
     return storage == LBM_STORE_F32 ? block_smem_bytes<float>() : block_smem_bytes<__half>();
 }
 
-// Resident blocks of the ensemble kernel on the current device for `smem` bytes.
-int ensemble_slots(size_t smem, cudaError_t* err) {
+template <int TW>
+static cudaError_t ensemble_attr() {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)block_smem_bytes<float, TW>());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+
+// Resident blocks of the ensemble kernel of tile width tile_x for `smem` bytes.
+int ensemble_slots(size_t smem, int tile_x, cudaError_t* err) {
     int dev = 0, sms = 0, occ = 0;
-    cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)block_smem_bytes<float>());
+    const bool wide = tile_x == kWideTileW;
+    cudaError_t e = wide ? ensemble_attr<kWideTileW>() : ensemble_attr<kBlockTileW>();
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel, kBlockTileW, smem);
+        e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kWideTileW>, kWideTileW, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kBlockTileW>, kBlockTileW,
+                                                                 smem);
     if (err) *err = e;
     return std::max(1, sms * occ);
 }
 
 cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, size_t smem,
-                                 cudaStream_t st) {
+                                 int tile_x, cudaStream_t st) {
     (void)cudaGetLastError();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)block_smem_bytes<float>());
+    if (tile_x == kWideTileW) {
+        cudaError_t e = ensemble_attr<kWideTileW>();
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        ensemble_step_kernel<kWideTileW><<<total_tiles, kWideTileW, smem, st>>>(d_members, n, parity);
+    } else {
+        cudaError_t e = ensemble_attr<kBlockTileW>();
+        if (e != cudaSuccess) return e;
+        ensemble_step_kernel<kBlockTileW><<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
     }
-    ensemble_step_kernel<<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
     return cudaGetLastError();
 }
 
@@ -1268,6 +1517,29 @@ static cudaError_t launch_dec(const StepLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_pair(const StepLaunch& L, cudaStream_t st) {
+    static int slots = 0;
+    if (slots == 0) {
+        const size_t smem = pair_smem_bytes<T>();
+        cudaError_t e = cudaFuncSetAttribute(step_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_pair_kernel<T>, kPairThreads, smem)) !=
+            cudaSuccess)
+            return e;
+        slots = std::max(1, sms * occ);
+    }
+    const Grid& g = L.grid;
+    const int gx = (g.nx + kWideTileW - 1) / kWideTileW;
+    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots));
+    step_pair_kernel<T><<<grid, kPairThreads, pair_smem_bytes<T>(), st>>>((const T*)L.fin, (T*)L.fout, g, L.phys,
+                                                                           L.flag);
+    return cudaGetLastError();
+}
+
 // Columns per block tile of the block-staged kernel: tile_x when it is 128 or 256;
 // otherwise 256 for 16-bit storage, and for FP32 when the 256-column tiles hold at
 // least kWideMinRows rows (tile_y, or the rows of the one-wave default).  Measured
@@ -1305,10 +1577,17 @@ static cudaError_t launch_step_t(const StepLaunch& L, int kernel, cudaStream_t s
         density_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, g, L.phys);
         collide_kernel<T><<<grid, kThreadsX, 0, st>>>((const T*)L.fin, L.psi, (T*)L.fout, g, L.phys, L.flag);
     } else if (kernel == LBM_KERNEL_STAGED) {
+        // 16-bit storage at the default width: the paired-column tile (same results bit
+        // for bit; equal at 1024x2048, 1.23x the 256-thread tile at 10000x5000)
+        if constexpr (IsShifted<T>::value)
+            if (L.tile_x == 0) return launch_pair<T>(L, st);
         int tw = 0;
         cudaError_t e = block_tile_width<T>(g, L.tile_x, L.tile_y, &tw);
         if (e != cudaSuccess) return e;
         return tw == kWideTileW ? launch_block<T, kWideTileW>(L, st) : launch_block<T, kBlockTileW>(L, st);
+    } else if (kernel == LBM_KERNEL_PAIRED) {
+        if constexpr (IsShifted<T>::value) return launch_pair<T>(L, st);
+        else return cudaErrorInvalidValue;
     } else if (kernel == LBM_KERNEL_DECOUPLED) {
         int tw = 0;
         cudaError_t e = block_tile_width<T>(g, L.tile_x, L.tile_y, &tw);

@@ -15,7 +15,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "liblbm.so"
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3, "pipe": 4, "decoupled": 5}
+KERNEL = {"fused": 0, "two_pass": 1, "staged": 2, "warp": 3, "pipe": 4, "decoupled": 5, "paired": 6}
 
 
 class LbmParams(C.Structure):
@@ -87,6 +87,7 @@ _PROTOS = {
     "lbm_ens_member": (C.c_int, [C.c_void_p, C.c_int32, _P(_h)]),
     "lbm_ens_diagnostics": (C.c_int, [C.c_void_p, _P(LbmDiag)]),
     "lbm_ens_tune": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_double)]),
+    "lbm_ens_tile_width": (C.c_int, [C.c_void_p, _P(C.c_int32)]),
     "lbm_ens_destroy": (None, [C.c_void_p]),
     "lbm_cnn_workspace_bytes": (C.c_int, [C.c_int32, C.c_int32, _P(C.c_size_t)]),
     "lbm_cnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
@@ -389,10 +390,20 @@ class Ensemble:
     def sync(self):
         _check(self.lib.lbm_ens_sync(self._e), "lbm_ens_sync")
 
-    def diagnostics(self) -> list[dict]:
+    def diagnostics(self, check: bool = True) -> list[dict]:
+        """Every member's diagnostics; with check=False an unstable member's status is
+        reported in its dict instead of raising."""
         out = (LbmDiag * len(self.params))()
-        _check(self.lib.lbm_ens_diagnostics(self._e, out), "lbm_ens_diagnostics")
+        st = self.lib.lbm_ens_diagnostics(self._e, out)
+        if check or st not in (LBM_OK, LBM_EUNSTABLE):
+            _check(st, "lbm_ens_diagnostics")
         return [diag_dict(d) for d in out]
+
+    @property
+    def tile_width(self) -> int:
+        v = C.c_int32()
+        _check(self.lib.lbm_ens_tile_width(self._e, C.byref(v)), "lbm_ens_tile_width")
+        return v.value
 
     def tune(self) -> tuple[int, float]:
         ty, ms = C.c_int32(), C.c_double()

@@ -24,18 +24,19 @@ MEMBERS = [
 ]
 
 
-def member_params(m, tile_y=0):
+def member_params(m, tile_y=0, tile_x=0):
     d = inputs.params(inputs.C0, crop_rows=5, g=1e-4)
     d.update(m)
-    return lbm.default_params(kernel="staged", tile_y=tile_y, **d)
+    return lbm.default_params(kernel="staged", tile_y=tile_y, tile_x=tile_x, **d)
 
 
 # tile_y 16: 55 tiles in one partial wave; tile_y 1: 854 one-row tiles for the 608
 # resident blocks of GB300, two waves of mixed storage types
-@pytest.mark.parametrize("tile_y", [16, 1])
-def test_ensemble_members_equal_solo_runs(gpu, tile_y):
-    params = [member_params(m, tile_y=tile_y) for m in MEMBERS]
+@pytest.mark.parametrize("tile_y,tile_x", [(16, 0), (1, 0), (16, 256), (5, 256)])
+def test_ensemble_members_equal_solo_runs(gpu, tile_y, tile_x):
+    params = [member_params(m, tile_y=tile_y, tile_x=tile_x) for m in MEMBERS]
     with lbm.Ensemble(params) as ens:
+        assert ens.tile_width == (256 if tile_x == 256 else 128)
         ens.step(73)                     # one 50-step graph + 23 single launches
         ens.sync()
         got = [m.populations() for m in ens.members]
@@ -64,6 +65,7 @@ def test_ensemble_tune_keeps_states(gpu):
         before = [m.populations() for m in ens.members]
         ty, ms = ens.tune()
         assert 12 <= ty <= 256 and ms > 0
+        assert ens.tile_width in (128, 256)
         after = [m.populations() for m in ens.members]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)

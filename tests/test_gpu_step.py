@@ -83,6 +83,25 @@ def test_tile_widths_give_identical_states(gpu, storage):
     assert np.array_equal(states[0], states[1]) and np.array_equal(states[1], states[2])
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("nx,ny,tile_y", [(600, 90, 0), (517, 64, 5), (255, 40, 1), (7, 16, 0)])
+def test_paired_kernel_equals_the_staged_one(gpu, storage, nx, ny, tile_y):
+    # two columns per thread (odd and ragged widths: a last column without its pair,
+    # ghost columns on both edges) give the block-staged kernel's states bit for bit
+    d = inputs.params(inputs.C0, nx=nx, ny=ny, crop_rows=3, g=1e-4, G_wall_B=0.1, wall_mode=1)
+    states = []
+    for kernel in ("staged", "paired"):
+        with lbm.Solver(kernel=kernel, storage=storage, tile_x=256, tile_y=tile_y, **d) as s:
+            s.step(25)
+            states.append(s.populations())
+    assert np.array_equal(states[0], states[1])
+
+
+def test_paired_kernel_is_for_16bit_storage(gpu):
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(kernel="paired", storage="f32", **inputs.params(inputs.C0, nx=64, ny=32, crop_rows=3))
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("tile_x,tile_y", [(0, 0), (128, 7), (256, 1)])
 def test_decoupled_kernel_equals_the_staged_one(gpu, storage, tile_x, tile_y):

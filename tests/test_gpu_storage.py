@@ -67,7 +67,7 @@ def test_storage_error_against_the_oracle(gpu, storage, reference):
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("kernel", ["fused", "two_pass", "staged", "warp", "pipe", "decoupled"])
+@pytest.mark.parametrize("kernel", ["fused", "two_pass", "staged", "warp", "pipe", "decoupled", "paired"])
 def test_one_step_of_the_16bit_storage(gpu, storage, kernel):
     # the state the storage holds (rounded) is read back and stepped by the oracle
     nx, ny = 150, 40
@@ -89,8 +89,8 @@ def test_one_step_of_the_16bit_storage(gpu, storage, kernel):
 def test_pure_phases_in_16bit_storage_stay_stable(gpu, storage):
     # G = 0 without minority: the absent component's density is exactly 0 in each
     # bulk, which 16-bit shifted storage cannot represent; its stochastic rounding
-    # makes it fluctuate by a few 1e-4 around 0, inside the guard's floor of -1 %
-    # (FP16) or -5 % (BF16) of rho0_s, and mass stays conserved
+    # makes it fluctuate by a few 1e-4 around 0 (within 1 % (FP16) or 5 % (BF16) of
+    # rho0_s, the guard's floor being -5 %), and mass stays conserved
     d = inputs.params(inputs.C0, G=0.0, minority=0.0, g=1e-4)
     with lbm.Solver(storage=storage, **d) as s:
         m0 = s.diagnostics()
