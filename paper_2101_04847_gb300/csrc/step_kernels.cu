@@ -1075,9 +1075,9 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
         else
             pull_block<T, TW>(sS, sC, sN, yo == 0, yo == g.ny - 1, kk, f);
     };
-    // densities of row yo into ring slot yo & 3 (16-bit storage holds h = f - w rho0)
-    auto densities = [&](int yo) {
-        const T *sS = stage_of(yo - 1), *sC = stage_of(yo), *sN = stage_of(yo + 1);
+    // densities of row yo into ring slot yo & 3 (16-bit storage holds h = f - w rho0),
+    // from the stages of rows yo - 1, yo, yo + 1
+    auto densities = [&](int yo, const T* sS, const T* sC, const T* sN) {
         const int sl = yo & 3;
         float f[2][9];
         pull_row(yo, sS, sC, sN, ka, f);
@@ -1098,23 +1098,40 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
         sR[sl][0][2 * t + 2] = 0.0f; sR[sl][1][2 * t + 2] = 0.0f;
         if (halo) { sR[sl][0][sh] = 0.0f; sR[sl][1][sh] = 0.0f; }
     };
-    // collide the site in ring column c (window column kk) of row y; out: its values
-    // with the stochastic rounding's bits added, to be rounded toward zero
-    auto site = [&](int y, const T* sS, const T* sC, const T* sN, int kk, int c, int x, float out[2][9]) {
-        float h[2][9];
-        pull_row(y, sS, sC, sN, kk, h);
+    // neighbour densities of the thread's first (b = 0) or second (b = 1) site on row y:
+    // ring columns 2t .. 2t + 3 of rows y - 1, y, y + 1 as two aligned float2 loads per
+    // row and component (consecutive lanes read consecutive 8-byte words)
+    auto neighbours = [&](int y, int b, Nbr& pA, Nbr& pB) {
         const int s0 = (y - 1) & 3, s1 = y & 3, s2 = (y + 1) & 3;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            Nbr& p = c == 0 ? pA : pB;
+            const float2 L0 = *reinterpret_cast<const float2*>(&sR[s0][c][2 * t]);
+            const float2 R0 = *reinterpret_cast<const float2*>(&sR[s0][c][2 * t + 2]);
+            const float2 L1 = *reinterpret_cast<const float2*>(&sR[s1][c][2 * t]);
+            const float2 R1 = *reinterpret_cast<const float2*>(&sR[s1][c][2 * t + 2]);
+            const float2 L2 = *reinterpret_cast<const float2*>(&sR[s2][c][2 * t]);
+            const float2 R2 = *reinterpret_cast<const float2*>(&sR[s2][c][2 * t + 2]);
+            if (b == 0) {   // ring column 2t + 1
+                p.W = L1.x; p.E = R1.x;
+                p.SW = L0.x; p.S = L0.y; p.SE = R0.x;
+                p.NW = L2.x; p.N = L2.y; p.NE = R2.x;
+            } else {        // ring column 2t + 2
+                p.W = L1.y; p.E = R1.y;
+                p.SW = L0.y; p.S = R0.x; p.SE = R0.y;
+                p.NW = L2.y; p.N = R2.x; p.NE = R2.y;
+            }
+        }
+    };
+    // collide the thread's site b (window column ka + b, column xa + b) of row y; out:
+    // its values with the stochastic rounding's bits added, to be rounded toward zero
+    auto site = [&](int y, const T* sS, const T* sC, const T* sN, int b, float out[2][9]) {
+        float h[2][9];
+        pull_row(y, sS, sC, sN, ka + b, h);
         Nbr pA, pB;
-        pA.E = sR[s1][0][c + 1]; pA.W = sR[s1][0][c - 1];
-        pA.N = sR[s2][0][c];     pA.S = sR[s0][0][c];
-        pA.NE = sR[s2][0][c + 1]; pA.NW = sR[s2][0][c - 1];
-        pA.SE = sR[s0][0][c + 1]; pA.SW = sR[s0][0][c - 1];
-        pB.E = sR[s1][1][c + 1]; pB.W = sR[s1][1][c - 1];
-        pB.N = sR[s2][1][c];     pB.S = sR[s0][1][c];
-        pB.NE = sR[s2][1][c + 1]; pB.NW = sR[s2][1][c - 1];
-        pB.SE = sR[s0][1][c + 1]; pB.SW = sR[s0][1][c - 1];
+        neighbours(y, b, pA, pB);
         collide_shifted(h, pA, pB, ph, y, g.ny, flag);
-        dither_site<T>(g, y, x, h, seed, out);
+        dither_site<T>(g, y, xa + b, h, seed, out);
     };
     auto ghost = [&](int y, int x, const float v[2][9]) {   // periodic copies of the two first / last columns
         if (x < 2 || x >= g.nx - 2) {
@@ -1128,21 +1145,33 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
 
     if (y0 > 0) {
         wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
-        densities(y0 - 1);
+        densities(y0 - 1, stage_of(y0 - 2), stage_of(y0 - 1), stage_of(y0));
     } else {
         zero_row(y0 - 1);
     }
     wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
-    densities(y0);
+    densities(y0, stage_of(y0 - 1), stage_of(y0), stage_of(y0 + 1));
     __syncthreads();
     if (t < 32) {
         fence_proxy_async_smem();
         for (; next <= rlast && next - kBlockStages <= y0 - 2; ++next) issue(next);
     }
+    // stage of row y (advanced by one per row, no division): rows y - 1 .. y + 2 sit in
+    // the stages beside it.  A row outside [rfirst, rlast] maps to some stage, but its
+    // pull is never read (bounce-back on the wall rows takes the centre row instead).
+    constexpr int S = kBlockStages;
+    constexpr size_t kStageElems = (size_t)18 * W;
+    int jy = y0 - rfirst;
     for (int y = y0; y < y1; ++y) {
+        const int jm = jy == 0 ? S - 1 : jy - 1;
+        const int jp = jy == S - 1 ? 0 : jy + 1;
+        const int jq = jp == S - 1 ? 0 : jp + 1;
+        const T* sS = stage + jm * kStageElems;
+        const T* sC = stage + jy * kStageElems;
+        const T* sN = stage + jp * kStageElems;
         if (y + 1 < g.ny) {
             wait_row(y + 2);
-            densities(y + 1);
+            densities(y + 1, sC, sN, stage + jq * kStageElems);
         } else {
             zero_row(y + 1);
         }
@@ -1154,12 +1183,11 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
             for (; next <= rlast && next - kBlockStages <= y - 2; ++next) issue(next);
         }
         if (own_a) {
-            const T *sS = stage_of(y - 1), *sC = stage_of(y), *sN = stage_of(y + 1);
             float va[2][9], vb[2][9];
-            site(y, sS, sC, sN, ka, 2 * t + 1, xa, va);
+            site(y, sS, sC, sN, 0, va);
             T* q = fout + (size_t)y * g.pitch + g.origin + xa;
             if (own_b) {
-                site(y, sS, sC, sN, ka + 1, 2 * t + 2, xa + 1, vb);
+                site(y, sS, sC, sN, 1, vb);
                 // one conversion and one 32-bit store per plane for the column pair
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
@@ -1175,6 +1203,7 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
             }
             ghost(y, xa, va);
         }
+        jy = jp;
     }
 }
 
@@ -1182,7 +1211,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPairThreads, 4)
 step_pair_kernel(const T* __restrict__ fin, T* __restrict__ fout, Grid g, Physics ph, int* flag) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ PairRingT<T> sR;
+    __shared__ __align__(16) PairRingT<T> sR;
     const int y0 = (int)(((long long)blockIdx.y * g.ny) / gridDim.y);
     const int y1 = (int)(((long long)(blockIdx.y + 1) * g.ny) / gridDim.y);
     const uint32_t seed = launch_seed(ph);
