@@ -390,7 +390,8 @@ lbm_status lbm_closure_train(lbm_closure* c, int32_t epochs, double lr, uint64_t
  * applied on the interface and not in either bulk.  Corrections keep each component's
  * mass and never halve a density.  Diagnostics of both runs at intervals + 1 times
  * into coarse_out / fine_out (the fine run is the reference and the fallback: if the
- * coarse run turns unstable its status is returned, fine_out stays valid). */
+ * coarse run turns unstable its status is returned, fine_out stays valid).  Each call
+ * starts both runs afresh, their density guards cleared. */
 lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fine_steps, int32_t intervals,
                                 int32_t use_net, lbm_diag* coarse_out, lbm_diag* fine_out);
 

@@ -1081,6 +1081,8 @@ lbm_status lbm_closure_evaluate(lbm_closure* c, uint64_t seed, int32_t warmup_fi
     CL_STATUS(lbm_step(c->fine, warmup_fine_steps));
     CL_STATUS(restrict_fine(c, c->raw));
     CL_STATUS(set_coarse(c, c->raw));
+    // a new coarse run: an earlier evaluation that tripped the guard leaves it raised
+    CL_TRY(lbm::handle_clear_guard(c->coarse), "clear coarse guard");
     CL_STATUS(lbm_diagnostics(c->coarse, &coarse_out[0]));
     CL_STATUS(lbm_diagnostics(c->fine, &fine_out[0]));
     for (int k = 1; k <= intervals; ++k) {

@@ -653,11 +653,12 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
         const int rr = min(max(r, rfirst), rlast);
         return stage + (size_t)((rr - rfirst) % kBlockStages) * 18 * W;
     };
-    auto pull_row = [&](int yo, int kk, float f[2][9]) {
+    // pull of row yo from the stages of rows yo - 1 (S), yo (C), yo + 1 (N)
+    auto pull_row = [&](int yo, const T* sS, const T* sC, const T* sN, int kk, float f[2][9]) {
         if (yo > 0 && yo < g.ny - 1)   // interior row (uniform over the block): no bounce-back selects
-            pull_block<T, TW>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), false, false, kk, f);
+            pull_block<T, TW>(sS, sC, sN, false, false, kk, f);
         else
-            pull_block<T, TW>(stage_of(yo - 1), stage_of(yo), stage_of(yo + 1), yo == 0, yo == g.ny - 1, kk, f);
+            pull_block<T, TW>(sS, sC, sN, yo == 0, yo == g.ny - 1, kk, f);
     };
     // densities of row yo into ring slot yo & 3 (zero for columns past nx); 16-bit
     // storage holds h = f - w rho0, whose sum is rho - rho0
@@ -665,14 +666,14 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
         if constexpr (IsShifted<T>::value) return sum9(f) + shift[s];
         else return sum9(f);
     };
-    auto densities = [&](int yo, float f[2][9]) {
-        pull_row(yo, k, f);
+    auto densities = [&](int yo, const T* sS, const T* sC, const T* sN, float f[2][9]) {
+        pull_row(yo, sS, sC, sN, k, f);
         const int sl = yo & 3;
         sR[sl][0][t + 1] = dens ? density(f[0], 0) : 0.0f;
         sR[sl][1][t + 1] = dens ? density(f[1], 1) : 0.0f;
         if (halo) {
             float fh[2][9];
-            pull_row(yo, kh, fh);
+            pull_row(yo, sS, sC, sN, kh, fh);
             sR[sl][0][sh] = density(fh[0], 0);
             sR[sl][1][sh] = density(fh[1], 1);
         }
@@ -681,14 +682,14 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     float fa[2][9], fb[2][9];
     if (y0 > 0) {   // densities of row y0 - 1 (zero on the virtual wall row)
         wait_row(y0 - 2); wait_row(y0 - 1); wait_row(y0);
-        densities(y0 - 1, fb);
+        densities(y0 - 1, stage_of(y0 - 2), stage_of(y0 - 1), stage_of(y0), fb);
     } else {
         const int sl = (y0 - 1) & 3;
         sR[sl][0][t + 1] = 0.0f; sR[sl][1][t + 1] = 0.0f;
         if (halo) { sR[sl][0][sh] = 0.0f; sR[sl][1][sh] = 0.0f; }
     }
     wait_row(y0 - 1); wait_row(y0); wait_row(y0 + 1);
-    densities(y0, fa);
+    densities(y0, stage_of(y0 - 1), stage_of(y0), stage_of(y0 + 1), fa);
     // everybody is past the prologue's reads of row y0 - 2: its stage can take row y0 + 3
     __syncthreads();
     if (t < 32) {
@@ -696,10 +697,16 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
         for (; next <= rlast && next - kBlockStages <= y0 - 2; ++next) issue(next);
     }
 
-    auto row = [&](int y, float cur[2][9], float nxt[2][9]) {
+    // jy: the stage of row y, advanced by one per row without a division.  Rows y .. y + 2
+    // sit in it and the two stages after it; a row beyond rlast maps to some stage, but
+    // its pull is not read (bounce-back on the top wall row takes the centre row instead).
+    constexpr size_t kStageElems = (size_t)18 * W;
+    auto row = [&](int y, int jy, float cur[2][9], float nxt[2][9]) {
         if (y + 1 < g.ny) {
+            const int jp = jy == kBlockStages - 1 ? 0 : jy + 1;
+            const int jq = jp == kBlockStages - 1 ? 0 : jp + 1;
             wait_row(y + 2);
-            densities(y + 1, nxt);
+            densities(y + 1, stage + jy * kStageElems, stage + jp * kStageElems, stage + jq * kStageElems, nxt);
         } else {
             const int sl = (y + 1) & 3;
             sR[sl][0][t + 1] = 0.0f; sR[sl][1][t + 1] = 0.0f;
@@ -732,9 +739,12 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
             }
         }
     };
+    int jy = y0 - rfirst;
     for (int y = y0; y < y1; y += 2) {
-        row(y, fa, fb);
-        if (y + 1 < y1) row(y + 1, fb, fa);
+        const int jn = jy == kBlockStages - 1 ? 0 : jy + 1;
+        row(y, jy, fa, fb);
+        if (y + 1 < y1) row(y + 1, jn, fb, fa);
+        jy = jn == kBlockStages - 1 ? 0 : jn + 1;
     }
 }
 

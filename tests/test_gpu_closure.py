@@ -400,3 +400,29 @@ def test_run_falls_back_to_the_fine_solver(gpu):
     # prolongation keep it; the fine steps conserve it)
     for s, k in ((0, "rhoA"), (1, "rhoB")):
         assert abs(got[s].sum() - start[k].sum()) <= 1e-5 * start[k].sum()
+
+
+def test_an_unstable_evaluation_does_not_spoil_the_next_one(gpu):
+    # velocity corrections ten thousand times too large trip the coarse run's density
+    # guard; the next evaluation starts a new coarse run and must give what a fresh
+    # closure gives (the guard is cleared, not left raised)
+    fresh = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        want = fresh.evaluate(seed=101, warmup=50, intervals=3, use_net=0)
+    finally:
+        fresh.close()
+    c = lbm.Closure(lbm.default_params(**FINE), interval=10, seed=0)
+    try:
+        _, _, p32, (mean, scale, _) = seeded_correction_inputs(c)
+        c.set_params(p32)
+        c.set_normalisation(mean, scale, np.array([3e-3, 3e-3, 40.0, 40.0], dtype=np.float32))
+        with pytest.raises(lbm.LbmError) as err:
+            c.evaluate(seed=101, warmup=50, intervals=2, use_net=4)
+        assert err.value.status == lbm.LBM_EUNSTABLE
+        got = c.evaluate(seed=101, warmup=50, intervals=3, use_net=0)
+    finally:
+        c.close()
+    for run in (0, 1):   # coarse and fine series
+        assert [d["E_k"] for d in got[run]] == [d["E_k"] for d in want[run]]
+        assert [d["h"] for d in got[run]] == [d["h"] for d in want[run]]
+
