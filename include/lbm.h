@@ -107,8 +107,11 @@ typedef struct {
                               * (one column per thread); 0 = chosen per grid: for 16-bit storage
                               * the paired-column tile (256 columns, two per thread, the
                               * LBM_KERNEL_PAIRED kernel), for FP32 256 when the 256-column tiles
-                              * are at least 64 rows tall, else 128.  Other kernels ignore it;
-                              * ensembles take 128 or 256 (lbm_ens_tune). */
+                              * are at least 64 rows tall, else 128.  Other kernels ignore it.
+                              * Ensembles (the first member's value): 128 or 256 columns, one
+                              * per thread, for every member; 0 = blocks of 128 threads, FP32
+                              * members in 128-column tiles and 16-bit members in paired
+                              * 256-column tiles (lbm_ens_tune picks among the three). */
     int32_t wall_mode;       /* pseudopotential beyond the walls in the Shan-Chen force (Section 2
                               * leaves it open): 0 = none (psi = 0 on the virtual rows y = -1 and
                               * y = ny); 1 = mirror (those rows hold the wall rows' own psi: a
@@ -307,13 +310,14 @@ lbm_status lbm_ens_member(lbm_ensemble* e, int32_t i, lbm_handle** out);
 /* Diagnostics of every member into out[0..n-1]; synchronises. */
 lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out);
 
-/* Pick the tile shape for the whole ensemble by timing candidates: tile widths of 128
- * and 256 columns (threads per block) times tile heights (0, the slot-filling
- * default, among them); states are kept.  tile_y receives the rows per tile in use.
- * The initial width is the first member's tile_x when it is 256, else 128. */
+/* Pick the tile shape for the whole ensemble by timing candidates: the three tile
+ * widths of lbm_params.tile_x (128, 256, 0 = paired 16-bit tiles) times tile heights
+ * (0, the slot-filling default, among them); states are kept.  tile_y receives the
+ * rows per tile in use.  The initial width is the first member's tile_x when it is
+ * 128 or 256, else 0. */
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y, double* ms_per_step);
 
-/* Columns per tile of the ensemble's launch (128 or 256). */
+/* Tile width of the ensemble's launch: 128, 256 or 0 (see lbm_params.tile_x). */
 lbm_status lbm_ens_tile_width(lbm_ensemble* e, int32_t* tile_x);
 
 void lbm_ens_destroy(lbm_ensemble* e);

@@ -33,7 +33,8 @@ struct lbm_ensemble {
     std::vector<lbm::EnsMember> table;
     lbm::EnsMember* d_table = nullptr;
     int total_tiles = 0;
-    int tile_x = lbm::kBlockTileW;   // columns per tile (and threads per block): 128 or 256
+    int tile_x = lbm::kEnsPaired;    // 128 or 256 columns per tile (one per thread), or
+                                     // kEnsPaired (FP32 128 columns, 16-bit paired 256)
     int tile_y = 0;       // requested rows per tile; 0: chosen from the device's block slots
     int rows = 0;         // rows per tile in use
     size_t smem = 0;      // dynamic shared memory per block (largest storage type present)
@@ -69,7 +70,8 @@ int auto_rows(const lbm_ensemble* e, int slots) {
         long long tiles = 0;
         for (lbm_handle* h : e->members) {
             int tx, ty;
-            tiles += tiles_of(lbm::handle_grid(h), e->tile_x, rows, &tx, &ty);
+            tiles += tiles_of(lbm::handle_grid(h), lbm::ensemble_tile_cols(lbm::handle_params(h).storage, e->tile_x),
+                              rows, &tx, &ty);
         }
         const long long waves = (tiles + slots - 1) / slots;
         const double score = (double)tiles / (double)(waves * slots) * rows / (rows + 3.0);
@@ -112,7 +114,8 @@ lbm_status ens_build_table(lbm_ensemble* e) {
         m.flag = lbm::handle_flag(h);
         m.storage = lbm::handle_params(h).storage;
         m.step_ctr = lbm::handle_step_counters(h);
-        const int tiles = tiles_of(m.grid, e->tile_x, e->rows, &m.tiles_x, &m.tiles_y);
+        const int tiles = tiles_of(m.grid, lbm::ensemble_tile_cols(m.storage, e->tile_x), e->rows, &m.tiles_x,
+                                   &m.tiles_y);
         m.tile_begin = begin;
         begin += tiles;
         e->table.push_back(m);
@@ -191,7 +194,8 @@ lbm_status lbm_ens_create(int32_t n, const lbm_params* params, void* cuda_stream
         e->own_stream = true;
     }
     e->tile_y = params[0].tile_y > 0 ? params[0].tile_y : 0;
-    e->tile_x = params[0].tile_x == lbm::kWideTileW ? lbm::kWideTileW : lbm::kBlockTileW;
+    e->tile_x = params[0].tile_x == lbm::kWideTileW || params[0].tile_x == lbm::kBlockTileW ? params[0].tile_x
+                                                                                             : lbm::kEnsPaired;
     for (int i = 0; i < n; ++i) {
         lbm_params p = params[i];
         p.kernel = LBM_KERNEL_STAGED;
@@ -270,7 +274,7 @@ lbm_status lbm_ens_diagnostics(lbm_ensemble* e, lbm_diag* out) {
 lbm_status lbm_ens_tune(lbm_ensemble* e, int32_t* tile_y_out, double* ms_out) {
     if (!e) return ens_fail(LBM_EINVAL, "ensemble is NULL");
     const int cand[] = {0, 12, 16, 20, 24, 32, 48, 64, 96};   // 0: the slot-filling default
-    const int widths[] = {lbm::kBlockTileW, lbm::kWideTileW};
+    const int widths[] = {lbm::kEnsPaired, lbm::kBlockTileW, lbm::kWideTileW};
     cudaEvent_t a, b;
     ENS_TRY(cudaEventCreate(&a), "event");
     ENS_TRY(cudaEventCreate(&b), "event");

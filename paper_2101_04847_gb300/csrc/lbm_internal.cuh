@@ -70,6 +70,9 @@ struct Grid {
 // ensemble kernel's and the narrow single-grid tile, and the wide single-grid tile.
 constexpr int kBlockTileW = 128;
 constexpr int kWideTileW = 256;
+// Ensemble tile width 0: blocks of 128 threads, FP32 members in tiles of 128 columns
+// (one per thread), 16-bit members in paired-column tiles of 256 (two per thread).
+constexpr int kEnsPaired = 0;
 
 struct StepLaunch {
     const void* fin;
@@ -91,7 +94,7 @@ struct EnsMember {
     int* flag;           // the member's guard flag
     int storage;         // lbm_storage
     uint32_t* step_ctr;  // the member's two time-step counters (see Physics)
-    int tiles_x;         // block tiles along x (128 columns each)
+    int tiles_x;         // block tiles along x (ensemble_tile_cols columns each)
     int tiles_y;         // block tiles along y (rows split evenly)
     int tile_begin;      // index of the member's first tile in the flat list
 };
@@ -99,6 +102,8 @@ struct EnsMember {
 // ensemble / tiling helpers (step_kernels.cu)
 int warp_tiles(const Grid& g, int tile_y, int* tiles_x);
 int default_tile_y();
+// columns of one ensemble tile of a member with this storage (tile_x 128, 256 or kEnsPaired)
+int ensemble_tile_cols(int storage, int tile_x);
 // dynamic shared memory of one block tile for a storage type
 size_t block_tile_smem_bytes(int storage, int tile_x);
 // resident blocks of the ensemble kernel on the current device with `smem` bytes each

@@ -1262,11 +1262,15 @@ step_block_timeout_kernel(const float* __restrict__ fin, float* __restrict__ fou
 // the member's grid, physics and storage type; no member waits for another, so
 // uneven grids need no barrier.
 // ---------------------------------------------------------------------------
-template <int TW>
+template <int TW, bool kPaired>
 __global__ void __launch_bounds__(TW, 512 / TW)
 ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ BlockRingT<TW> sR;
+    // density ring: the block tile's, or with kPaired also the paired tile's (16-bit members)
+    constexpr size_t kRing = kPaired && sizeof(PairRingT<__half>) > sizeof(BlockRingT<TW>) ? sizeof(PairRingT<__half>)
+                                                                                         : sizeof(BlockRingT<TW>);
+    __shared__ __align__(16) unsigned char ring[kRing];
+    BlockRingT<TW>& sR = *reinterpret_cast<BlockRingT<TW>*>(ring);
     const int tile = blockIdx.x;
     int lo = 0, hi = n - 1;   // last member whose first tile is <= tile
     while (lo < hi) {
@@ -1288,12 +1292,20 @@ ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     advance_step(ph, local == 0 && threadIdx.x == 0);
     switch (M.storage) {
         case LBM_STORE_F16:
-            block_tile<__half, TW>((const __half*)fin, (__half*)fout, M.grid, ph, tx * TW, y0, y1, dsm, sR, seed,
-                                   M.flag);
+            if constexpr (kPaired)
+                pair_tile<__half>((const __half*)fin, (__half*)fout, M.grid, ph, tx * kWideTileW, y0, y1, dsm,
+                                  *reinterpret_cast<PairRingT<__half>*>(ring), seed, M.flag);
+            else
+                block_tile<__half, TW>((const __half*)fin, (__half*)fout, M.grid, ph, tx * TW, y0, y1, dsm, sR, seed,
+                                       M.flag);
             break;
         case LBM_STORE_BF16:
-            block_tile<__nv_bfloat16, TW>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph, tx * TW, y0,
-                                          y1, dsm, sR, seed, M.flag);
+            if constexpr (kPaired)
+                pair_tile<__nv_bfloat16>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph, tx * kWideTileW,
+                                         y0, y1, dsm, *reinterpret_cast<PairRingT<__nv_bfloat16>*>(ring), seed, M.flag);
+            else
+                block_tile<__nv_bfloat16, TW>((const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, M.grid, ph, tx * TW, y0,
+                                              y1, dsm, sR, seed, M.flag);
             break;
         default:
             block_tile<float, TW>((const float*)fin, (float*)fout, M.grid, ph, tx * TW, y0, y1, dsm, sR, seed,
@@ -1301,18 +1313,27 @@ ensemble_step_kernel(const EnsMember* __restrict__ members, int n, int parity) {
     }
 }
 
+int ensemble_tile_cols(int storage, int tile_x) {
+    if (tile_x == kEnsPaired) return storage == LBM_STORE_F32 ? kBlockTileW : kWideTileW;
+    return tile_x;
+}
+
 size_t block_tile_smem_bytes(int storage, int tile_x) {
+    if (tile_x == kEnsPaired)
+        return storage == LBM_STORE_F32 ? block_smem_bytes<float>() : pair_smem_bytes<__half>();
     if (tile_x == kWideTileW)
         return storage == LBM_STORE_F32 ? block_smem_bytes<float, kWideTileW>() : block_smem_bytes<__half, kWideTileW>();
     return storage == LBM_STORE_F32 ? block_smem_bytes<float>() : block_smem_bytes<__half>();
 }
 
-template <int TW>
+template <int TW, bool kPaired>
 static cudaError_t ensemble_attr() {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)block_smem_bytes<float, TW>());
+        const size_t smem = kPaired ? std::max(block_smem_bytes<float, TW>(), pair_smem_bytes<__half>())
+                                    : block_smem_bytes<float, TW>();
+        cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel<TW, kPaired>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1322,14 +1343,22 @@ static cudaError_t ensemble_attr() {
 // Resident blocks of the ensemble kernel of tile width tile_x for `smem` bytes.
 int ensemble_slots(size_t smem, int tile_x, cudaError_t* err) {
     int dev = 0, sms = 0, occ = 0;
-    const bool wide = tile_x == kWideTileW;
-    cudaError_t e = wide ? ensemble_attr<kWideTileW>() : ensemble_attr<kBlockTileW>();
+    cudaError_t e = tile_x == kWideTileW ? ensemble_attr<kWideTileW, false>()
+                    : tile_x == kEnsPaired ? ensemble_attr<kBlockTileW, true>()
+                                           : ensemble_attr<kBlockTileW, false>();
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kWideTileW>, kWideTileW, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kBlockTileW>, kBlockTileW,
-                                                                 smem);
+    if (e == cudaSuccess) {
+        if (tile_x == kWideTileW)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kWideTileW, false>, kWideTileW,
+                                                              smem);
+        else if (tile_x == kEnsPaired)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kBlockTileW, true>, kBlockTileW,
+                                                              smem);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ensemble_step_kernel<kBlockTileW, false>,
+                                                              kBlockTileW, smem);
+    }
     if (err) *err = e;
     return std::max(1, sms * occ);
 }
@@ -1337,14 +1366,16 @@ int ensemble_slots(size_t smem, int tile_x, cudaError_t* err) {
 cudaError_t launch_ensemble_step(const EnsMember* d_members, int n, int total_tiles, int parity, size_t smem,
                                  int tile_x, cudaStream_t st) {
     (void)cudaGetLastError();
+    cudaError_t e = cudaSuccess;
     if (tile_x == kWideTileW) {
-        cudaError_t e = ensemble_attr<kWideTileW>();
-        if (e != cudaSuccess) return e;
-        ensemble_step_kernel<kWideTileW><<<total_tiles, kWideTileW, smem, st>>>(d_members, n, parity);
+        if ((e = ensemble_attr<kWideTileW, false>()) != cudaSuccess) return e;
+        ensemble_step_kernel<kWideTileW, false><<<total_tiles, kWideTileW, smem, st>>>(d_members, n, parity);
+    } else if (tile_x == kEnsPaired) {
+        if ((e = ensemble_attr<kBlockTileW, true>()) != cudaSuccess) return e;
+        ensemble_step_kernel<kBlockTileW, true><<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
     } else {
-        cudaError_t e = ensemble_attr<kBlockTileW>();
-        if (e != cudaSuccess) return e;
-        ensemble_step_kernel<kBlockTileW><<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
+        if ((e = ensemble_attr<kBlockTileW, false>()) != cudaSuccess) return e;
+        ensemble_step_kernel<kBlockTileW, false><<<total_tiles, kBlockTileW, smem, st>>>(d_members, n, parity);
     }
     return cudaGetLastError();
 }
@@ -1480,12 +1511,12 @@ __global__ void push_from_host_kernel(const V* __restrict__ S, Grid g, float sA,
 // ---------------------------------------------------------------------------
 // Row tiles of the block-staged kernel: tile_y > 0 asks for at most tile_y rows per
 // tile; 0 fills the device's resident block slots exactly once (one wave, every SM
-// equally loaded) unless that leaves fewer than kMinTileRows rows per tile.
-int block_tiles_y(int ny, int tiles_x, int tile_y, int slots) {
-    constexpr int kMinTileRows = 16;
+// equally loaded) unless that leaves fewer than min_rows rows per tile.
+constexpr int kMinTileRows = 16;   // shortest default tile of the one-column-per-thread tiles
+int block_tiles_y(int ny, int tiles_x, int tile_y, int slots, int min_rows) {
     if (tile_y > 0) return (ny + tile_y - 1) / tile_y;
     const int per_wave = std::max(1, slots / tiles_x);
-    const int fit = std::max(1, ny / kMinTileRows);
+    const int fit = std::max(1, ny / min_rows);
     return std::min(per_wave, fit);
 }
 
@@ -1518,7 +1549,7 @@ static cudaError_t launch_block(const StepLaunch& L, cudaStream_t st) {
     cudaError_t e = block_slots<T, TW>(&slots);
     if (e != cudaSuccess) return e;
     const int gx = (g.nx + TW - 1) / TW;
-    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots));
+    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots, kMinTileRows));
     step_block_kernel<T, TW><<<grid, TW, block_smem_bytes<T, TW>(), st>>>((const T*)L.fin, (T*)L.fout, g, L.phys,
                                                                            L.flag);
     return cudaGetLastError();
@@ -1551,7 +1582,7 @@ static cudaError_t launch_dec(const StepLaunch& L, cudaStream_t st) {
     cudaError_t e = dec_slots<T, TW>(&slots);
     if (e != cudaSuccess) return e;
     const int gx = (g.nx + TW - 1) / TW;
-    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots));
+    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots, kMinTileRows));
     step_dec_kernel<T, TW><<<grid, TW, dec_smem_bytes<T, TW>(), st>>>((const T*)L.fin, (T*)L.fout, g, L.phys, L.flag);
     return cudaGetLastError();
 }
@@ -1573,7 +1604,9 @@ static cudaError_t launch_pair(const StepLaunch& L, cudaStream_t st) {
     }
     const Grid& g = L.grid;
     const int gx = (g.nx + kWideTileW - 1) / kWideTileW;
-    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots));
+    // tiles down to 8 rows so that the wave is full: at 1024x2048 152 x 4 tiles of
+    // 13-14 rows run 11 % faster than 128 x 4 of 16 (measured with tile_y 14)
+    dim3 grid(gx, block_tiles_y(g.ny, gx, L.tile_y, slots, 8));
     step_pair_kernel<T><<<grid, kPairThreads, pair_smem_bytes<T>(), st>>>((const T*)L.fin, (T*)L.fout, g, L.phys,
                                                                            L.flag);
     return cudaGetLastError();
@@ -1601,7 +1634,7 @@ static cudaError_t block_tile_width(const Grid& g, int tile_x, int tile_y, int* 
     cudaError_t e = block_slots<T, kWideTileW>(&slots);
     if (e != cudaSuccess) return e;
     const int gx = (g.nx + kWideTileW - 1) / kWideTileW;
-    const int rows = tile_y > 0 ? tile_y : g.ny / block_tiles_y(g.ny, gx, 0, slots);
+    const int rows = tile_y > 0 ? tile_y : g.ny / block_tiles_y(g.ny, gx, 0, slots, kMinTileRows);
     *tw = rows >= kWideMinRows ? kWideTileW : kBlockTileW;
     return cudaSuccess;
 }

@@ -30,13 +30,14 @@ def member_params(m, tile_y=0, tile_x=0):
     return lbm.default_params(kernel="staged", tile_y=tile_y, tile_x=tile_x, **d)
 
 
-# tile_y 16: 55 tiles in one partial wave; tile_y 1: 854 one-row tiles for the 608
-# resident blocks of GB300, two waves of mixed storage types
-@pytest.mark.parametrize("tile_y,tile_x", [(16, 0), (1, 0), (16, 256), (5, 256)])
+# tile_y 16: one partial wave; tile_y 1 (and 3): more one-row tiles than GB300's
+# resident blocks (700 at tile_x 0, 854 at 128 for 608 slots), two waves of mixed
+# storage types; tile_x 0 runs the 16-bit members in paired 256-column tiles
+@pytest.mark.parametrize("tile_y,tile_x", [(16, 0), (1, 0), (16, 128), (3, 128), (16, 256), (5, 256)])
 def test_ensemble_members_equal_solo_runs(gpu, tile_y, tile_x):
     params = [member_params(m, tile_y=tile_y, tile_x=tile_x) for m in MEMBERS]
     with lbm.Ensemble(params) as ens:
-        assert ens.tile_width == (256 if tile_x == 256 else 128)
+        assert ens.tile_width == tile_x   # 0: paired tiles for the 16-bit members
         ens.step(73)                     # one 50-step graph + 23 single launches
         ens.sync()
         got = [m.populations() for m in ens.members]
@@ -65,7 +66,7 @@ def test_ensemble_tune_keeps_states(gpu):
         before = [m.populations() for m in ens.members]
         ty, ms = ens.tune()
         assert 12 <= ty <= 256 and ms > 0
-        assert ens.tile_width in (128, 256)
+        assert ens.tile_width in (0, 128, 256)
         after = [m.populations() for m in ens.members]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)
