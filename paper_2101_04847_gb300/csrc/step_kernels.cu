@@ -701,11 +701,12 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
     // sit in it and the two stages after it; a row beyond rlast maps to some stage, but
     // its pull is not read (bounce-back on the top wall row takes the centre row instead).
     constexpr size_t kStageElems = (size_t)18 * W;
-    auto row = [&](int y, int jy, float cur[2][9], float nxt[2][9]) {
+    // pq: the phase of the wait for row y + 2 in stage jq
+    auto row = [&](int y, int jy, uint32_t pq, float cur[2][9], float nxt[2][9]) {
         if (y + 1 < g.ny) {
             const int jp = jy == kBlockStages - 1 ? 0 : jy + 1;
             const int jq = jp == kBlockStages - 1 ? 0 : jp + 1;
-            wait_row(y + 2);
+            if (y + 2 <= rlast) mbar_wait(&bar[jq], pq, flag, kWithhold ? kTestWaitLimit : kWaitLimit);
             densities(y + 1, stage + jy * kStageElems, stage + jp * kStageElems, stage + jq * kStageElems, nxt);
         } else {
             const int sl = (y + 1) & 3;
@@ -739,11 +740,17 @@ __device__ __forceinline__ void block_tile(const T* __restrict__ fin, T* __restr
             }
         }
     };
+    // row r waits for fill (r - rfirst) / kBlockStages of its stage: the phase flips
+    // whenever the waited row's stage wraps to 0, i.e. after a row whose own stage is
+    // kBlockStages - 3
     int jy = y0 - rfirst;
+    uint32_t pq = (uint32_t)(((y0 + 2 - rfirst) / kBlockStages) & 1);
     for (int y = y0; y < y1; y += 2) {
         const int jn = jy == kBlockStages - 1 ? 0 : jy + 1;
-        row(y, jy, fa, fb);
-        if (y + 1 < y1) row(y + 1, jn, fb, fa);
+        row(y, jy, pq, fa, fb);
+        pq ^= (uint32_t)(jy == kBlockStages - 3);
+        if (y + 1 < y1) row(y + 1, jn, pq, fb, fa);
+        pq ^= (uint32_t)(jn == kBlockStages - 3);
         jy = jn == kBlockStages - 1 ? 0 : jn + 1;
     }
 }
@@ -1172,6 +1179,7 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
     constexpr int S = kBlockStages;
     constexpr size_t kStageElems = (size_t)18 * W;
     int jy = y0 - rfirst;
+    uint32_t pq = (uint32_t)(((y0 + 2 - rfirst) / S) & 1);   // phase of the wait for row y + 2
     for (int y = y0; y < y1; ++y) {
         const int jm = jy == 0 ? S - 1 : jy - 1;
         const int jp = jy == S - 1 ? 0 : jy + 1;
@@ -1180,7 +1188,7 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
         const T* sC = stage + jy * kStageElems;
         const T* sN = stage + jp * kStageElems;
         if (y + 1 < g.ny) {
-            wait_row(y + 2);
+            if (y + 2 <= rlast) mbar_wait(&bar[jq], pq, flag);
             densities(y + 1, sC, sN, stage + jq * kStageElems);
         } else {
             zero_row(y + 1);
@@ -1213,6 +1221,7 @@ __device__ __forceinline__ void pair_tile(const T* __restrict__ fin, T* __restri
             }
             ghost(y, xa, va);
         }
+        pq ^= (uint32_t)(jy == S - 3);   // row y + 3 sits in stage jy + 3: a new fill once it wraps to 0
         jy = jp;
     }
 }
