@@ -9,8 +9,10 @@ advances both components).  Population buffers (2 x 151 MB) exceed the 129 MB
 L2, so no separate L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--storage f32|f16|bf16] [--kernel staged|warp|pipe|fused|two_pass]
+                  [--storage f32|f16|bf16]
+                  [--kernel staged|paired|decoupled|warp|pipe|fused|two_pass]
                   [--tile-y T] [--nx NX --ny NY] [--ensemble M] [--storage-study STEPS]
+                  [--paper-case STEPS] [--closure-accuracy] [--closure] [--no-extra-lines]
 
 --impl reference times the FP64 CPU oracle on the host on a bounded sample of
 the same workload.  With torchrun (N > 1) every rank advances its own
@@ -43,14 +45,23 @@ def workload(args) -> dict:
                 n_modes=8, amp=2.0, width=1.5, minority=0.08, crop_rows=10)
 
 
+def l2_note(buffer_bytes: int) -> str:
+    """How the timed steps relate to the 129 MB L2: each LB step reads one population
+    buffer and writes the other, so the two together are what could stay cached."""
+    both = 2 * buffer_bytes
+    size = f"two population buffers of {buffer_bytes / 1e6:.0f} MB each, {both / 1e6:.0f} MB together, vs 129 MB L2"
+    if both > 129e6:
+        return f"inputs larger than L2 ({size}; each LB step reads one buffer and writes the other)"
+    return f"inputs fit in L2 ({size}): no L2 flush between steps, so this is not a DRAM-bound figure"
+
+
 def config_of(args, n_gpus) -> dict:
     return {
         "workload": f"{args.nx}x{args.ny} two-component D2Q9 Shan-Chen Rayleigh-Taylor, G=1.4, tau=1, "
                     f"{args.storage} populations, diagnostics every {LB_STEPS_PER_STEP} steps",
         "nx": args.nx, "ny": args.ny, "lb_steps_per_step": LB_STEPS_PER_STEP,
         "storage": args.storage, "kernel": args.kernel, "tile_y": args.tile_y,
-        "l2": "inputs larger than L2 (two population buffers of "
-              f"{args.nx * args.ny * BYTES_PER_SITE[args.storage] // 2 / 1e6:.0f} MB each vs 129 MB L2)",
+        "l2": l2_note(args.nx * args.ny * BYTES_PER_SITE[args.storage] // 2),
         "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single",
     }
 
@@ -418,7 +429,8 @@ def run_ensemble(args):
                                   else "from 512x1024/1024x2048/2048x4096")
                                + ", G from 0/1.2/1.4, FP32 or FP16 storage, one launch per LB step",
                    "members": [f"{m['nx']}x{m['ny']} G={m['G']} {m['storage']}" for m in members],
-                   "lb_steps_per_step": lb_steps, "tile_y": tile_y, "tile_x": tile_x},
+                   "lb_steps_per_step": lb_steps, "tile_y": tile_y, "tile_x": tile_x,
+                   "l2": l2_note(bytes_per_update // 2)},
         "sequential": {"value": round(seq, 1), "unit": "MLUPS", "speedup": round(agg / seq, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "kernel": "ensemble_step_kernel",
