@@ -263,3 +263,37 @@ def test_full_size_grid_initial_rows_and_conservation(gpu):
     for k in ("mass_A", "mass_B"):
         assert abs(m1[k] - m0[k]) <= 1e-6 * m0[k]
     assert np.isfinite(m1["E_k"]) and m1["E_k"] > 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_full_size_one_step_on_sampled_rows(gpu, storage):
+    # 10000 x 5000 in the launch configuration the benchmark times (FP32: the
+    # 256-column tiles the grid's default picks; FP16: the paired tile), 30 steps in:
+    # one more step on sampled rows against the oracle.  A row's update reads the
+    # rows within two of it only, so the oracle steps the band of rows y - 2 .. y + 2
+    # (cut to the grid at the walls); the band's own edges act as walls there, which
+    # changes its outer rows but not row y
+    d = inputs.params(inputs.C2, seed=6)
+    p = oracle_params(d)
+    rows = [0, 1, 2, 2470, 2500, 2531, 4997, 4999]
+    shape = (2, 9, d["ny"], d["nx"])
+    with lbm.Solver(storage=storage, **d) as s:
+        s.step(30)
+        f = s.populations(np.empty(shape, dtype=np.float32))
+        bands = {y: f[:, :, max(0, y - 2):min(d["ny"], y + 3)].astype(np.float64) for y in rows}
+        s.step(1)
+        s.populations(f)
+    got = {y: f[:, :, y].astype(np.float64) for y in rows}
+    del f
+    rho0 = np.array([d["mass_A"] * (1 + d["minority"]) / 2, d["mass_B"] * (1 + d["minority"]) / 2])
+    for y in rows:
+        lo = max(0, y - 2)
+        band = bands[y]
+        pb = O.Params(**{**p.__dict__, "ny": band.shape[2]})
+        ref = O.step(band, pb, 1)[:, :, y - lo]
+        err = float(np.max(np.abs(got[y] - ref)))
+        if storage == "f32":
+            assert err <= 2e-6 * np.max(np.abs(ref)), (y, err)
+        else:   # one spacing of the stored shifted values (stochastic rounding), as in the one-step storage test
+            h = ref - rho0[:, None, None] * O.W[None, :, None]
+            assert err <= 2.0 ** -10 * np.max(np.abs(h)) + 1e-6 * np.max(np.abs(ref)), (y, err)
