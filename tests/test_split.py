@@ -116,3 +116,21 @@ def test_two_gloo_ranks_equal_the_whole_grid(use_product):
         assert pr.exitcode == 0
     got = np.concatenate([o for _, o in out], axis=-1)
     assert np.array_equal(got, whole(O.Params(**PARAMS)))
+
+
+def test_a_five_row_band_steps_its_centre_row_exactly():
+    # the full-size parity test steps only the band of rows y - 2 .. y + 2 around a
+    # sampled row y (cut to the grid at the walls): the band's own edges act as walls,
+    # which changes its outer rows but not row y
+    p = O.Params(**PARAMS)
+    f = whole(p)
+    full = O.step(f, p, 1)
+    for y in (0, 1, 2, 15, 16, p.ny - 2, p.ny - 1):
+        lo = max(0, y - 2)
+        band = f[:, :, lo:min(p.ny, y + 3)]
+        got = O.step(band, p.with_(ny=band.shape[2]), 1)[:, :, y - lo]
+        assert np.array_equal(got, full[:, :, y]), y
+    # a band of three rows is too narrow: the centre row then differs
+    y = 16
+    narrow = O.step(f[:, :, y - 1:y + 2], p.with_(ny=3), 1)[:, :, 1]
+    assert not np.array_equal(narrow, full[:, :, y])
