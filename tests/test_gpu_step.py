@@ -232,6 +232,25 @@ def test_bench_configuration_one_step_full_grid(gpu, kernel, tile_x):
     assert rel_err(got, ref) < 2e-6
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_bench_configuration_one_step_full_grid_16bit(gpu, storage):
+    # 1024 x 2048 with 16-bit storage in the launch configuration the benchmark times
+    # (the paired tile, 4 x 152 tiles): one step from the stored (rounded) state
+    # against the oracle, within one spacing of the stored shifted values
+    d = inputs.params(inputs.C1, seed=2)
+    p = oracle_params(d)
+    with lbm.Solver(storage=storage, **d) as s:
+        s.step(20)
+        f = s.populations()
+        s.step(1)
+        got = s.populations()
+    ref = O.step(f, p, 1)
+    rho0 = np.array([d["mass_A"] * (1 + d["minority"]) / 2, d["mass_B"] * (1 + d["minority"]) / 2])
+    h = ref - rho0[:, None, None, None] * O.W[None, :, None, None]
+    bits = {"f16": 10, "bf16": 7}[storage]
+    assert float(np.max(np.abs(got - ref))) <= 2.0 ** -bits * np.max(np.abs(h)) + 1e-6 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("kernel", ["fused", "staged"])
 def test_bench_configuration_mass_conservation(gpu, kernel):
     d = inputs.params(inputs.C1, seed=4)
